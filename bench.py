@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark: ENO-MR cell-updates/s per RK stage on one GB300.
+
+Workload: 2D Euler (gamma = 1.4) four-quadrant Riemann problem on [0,1]^2,
+interface at (0.8, 0.8), quadrant states drawn with seed = rank, 4096^2 cells,
+ENO-MR order 9, transmissive boundaries, SSP-RK3 with the CFL 0.5 step
+computed on the device.  One benchmark step = one SSP-RK3 step (3 stages).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores instead (test infrastructure, not the product path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ENO-MR cell-updates/s per RK stage"
+UNIT = "cell-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--order", type=int, default=9)
+    ap.add_argument("--cfl", type=float, default=0.5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    return ap.parse_args()
+
+
+def config(a):
+    return {"workload": "euler2d_quadrant_riemann", "grid": [a.n, a.n], "order": a.order,
+            "cfl": a.cfl, "bc": "transmissive", "time_integrator": "SSP-RK3",
+            "step": "one SSP-RK3 step = 3 RK stages", "seed": "rank",
+            "l2": "inputs larger than L2 (one state is %.0f MB)" % (4 * 8 * a.n * a.n / 1e6)}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic FP64 work of one sweep launch (counted per interface; an FMA is
+# two flops, an add, multiply, divide or square root one)
+# ---------------------------------------------------------------------------
+def sweep_flops(order, C, sel, n_interfaces):
+    """Flops of one Euler sweep: per interface the Roe average and scaled
+    eigenvectors (28), per field the projection of the 2g-cell window
+    (40 per cell for C = 4: 20 FMAs for U and F; 24 for C = 3), the split
+    (2 FMAs per window value and side), per window: baseline indicator (8),
+    the indicators of the tested candidates up to the chosen one (2|S|-1
+    each; none when IS_0 = 0), the reconstruction on the chosen stencil
+    (2|S|-1) or the minmod fma (2), and the back-projection (C == 4: 20, C == 3: 14).  sel: the
+    selection histogram counts[T+3] over all windows of the launch."""
+    import oracle  # table sizes only
+    g = (order + 1) // 2
+    T = oracle.num_tested(order)
+    sizes = [oracle.candidate(order, t)[0] + oracle.candidate(order, t)[1] + 1 for t in range(T)]
+    proj = (40 if C == 4 else 24) * 2 * g
+    split = C * 2 * 2 * (2 * g - 1)
+    per_iface = 28 + proj + split + (20 if C == 4 else 14)
+    flops = per_iface * n_interfaces
+    walk_cum = np.cumsum([2 * s - 1 for s in sizes])
+    counts = np.asarray(sel, dtype=np.float64)
+    for t in range(T):
+        flops += counts[t] * (8 + walk_cum[t] + 2 * sizes[t] - 1)
+    # minmod outcomes: S(0,1) and S(1,0) come after a full walk; S(0,0) is
+    # counted as the IS_0 = 0 shortcut (lower bound)
+    flops += (counts[T] + counts[T + 1]) * (8 + walk_cum[-1] + 2)
+    flops += counts[T + 2] * (8 + 2)
+    return float(flops)
+
+
+def main_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2311_15504_gb300 import enomr, workloads
+
+    n, R = a.n, a.order
+    U0, dx, dy = workloads.riemann2d(n, n, seed=rank)
+    s = enomr.Solver(enomr.EULER, (n, n), order=R, dx=dx, dy=dy, bc=enomr.TRANSMISSIVE,
+                     device=dev)
+    U = torch.from_numpy(U0).to(dev)
+    for _ in range(a.warmup):
+        s.step(U, 0.0, a.cfl)
+    U.copy_(torch.from_numpy(U0))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    s.profile_begin(1, 3 * a.steps)  # x sweep: timed live during the run
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        s.step(U, 0.0, a.cfl)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    nx_launch, x_ms = s.profile_end()
+    s.check_status()
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max = float(t.item())
+    cells = n * n
+    value = world * cells * 3 * a.steps / (ms_max * 1e-3)
+    launches_per_step = 1 + 4 + 2 * 3  # dt, 4 alpha reductions, 2 sweeps x 3 stages
+
+    extras = {}
+    if rank == 0 and not a.no_extras:
+        # y sweep, timed over the same number of steps right after the run
+        Uy = torch.from_numpy(U0).to(dev)
+        s.profile_begin(2, 3 * a.steps)
+        for _ in range(a.steps):
+            s.step(Uy, 0.0, a.cfl)
+        ny_launch, y_ms = s.profile_end()
+        s.profile_begin(3, 4 * a.steps)
+        for _ in range(a.steps):
+            s.step(Uy, 0.0, a.cfl)
+        na_launch, a_ms = s.profile_end()
+        # selection histogram of the final state: algorithmic work of a sweep
+        T = enomr.num_tested(R)
+        sel = s.selection(U)
+        nsx = 8 * n * (n + 1)
+        hx = torch.bincount(sel[:nsx].long(), minlength=T + 3).cpu().numpy()
+        hy = torch.bincount(sel[nsx:].long(), minlength=T + 3).cpu().numpy()
+        fl_x = sweep_flops(R, 4, hx, n * (n + 1))
+        fl_y = sweep_flops(R, 4, hy, n * (n + 1))
+        fp64_peak, _ = enomr.probe_fp64_fma(iters=20000, device=dev)
+        x_avg = x_ms / max(nx_launch, 1)
+        y_avg = y_ms / max(ny_launch, 1)
+        dom, avg, fl = ("x_sweep", x_avg, fl_x) if x_avg >= y_avg else ("y_sweep", y_avg, fl_y)
+        achieved = fl / (avg * 1e-3) / 1e12
+        extras["roofline"] = {
+            "bound": "alu", "pipe": "fp64", "kernel": f"k_sweep<{R},4,{0 if dom == 'x_sweep' else 1}>",
+            "achieved": round(achieved, 4), "peak": round(fp64_peak / 1e12, 4),
+            "unit": "TFLOP/s", "frac": round(achieved / (fp64_peak / 1e12), 4),
+            "peak_source": "measured live: enomr_probe_fp64_fma (8 fma chains/thread, all SMs)",
+            "traffic": None,
+            "avg_launch_ms": round(avg, 4), "algorithmic_flops_per_launch": fl,
+            "x_sweep_ms": round(x_avg, 4), "y_sweep_ms": round(y_avg, 4),
+            "alpha_ms": round(a_ms / max(na_launch, 1), 4)}
+        extras["selection_histogram_x"] = hx.tolist()
+        # end to end through the public API with host buffers
+        Uh_in = torch.from_numpy(U0).pin_memory()
+        Uh_out = torch.empty_like(Uh_in).pin_memory()
+        Ue = torch.empty_like(U)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            Ue.copy_(Uh_in, non_blocking=True)
+            s.step(Ue, 0.0, a.cfl)
+            Uh_out.copy_(Ue, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        extras["e2e"] = {"value": cells * 3 * a.steps / e2e_s, "unit": UNIT,
+                         "h2d_bytes_per_step": Uh_in.numel() * 8,
+                         "d2h_bytes_per_step": Uh_out.numel() * 8}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64", "data": "synthetic (seeded four-quadrant Riemann states)",
+               "config": config(a), "clocks": clocks,
+               "gpu_launches": launches_per_step * a.steps}
+        out.update(extras)
+        if not a.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(a)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (test infrastructure)
+# ---------------------------------------------------------------------------
+def _oracle_problem(a, m):
+    """The same workload on an m x m grid (m = n: the full grid)."""
+    import oracle
+    from paper_2311_15504_gb300 import workloads
+    U0, dx, dy = workloads.riemann2d(m, m, seed=0)
+    P = oracle.Problem(oracle.EQ_EULER2D, a.order, m, m, dx=dx, dy=dy,
+                       bc=oracle.BC_TRANSMISSIVE)
+    return P, U0
+
+
+def _oracle_rate_estimate(a):
+    """seconds per cell of one oracle RHS with all threads (512^2 probe)."""
+    P, U0 = _oracle_problem(a, 512)
+    t0 = time.perf_counter()
+    P.rhs(U0)
+    return (time.perf_counter() - t0) / (512 * 512)
+
+
+def cpu_baseline(a, budget_s=20.0):
+    import oracle
+    per_cell = _oracle_rate_estimate(a)
+    m = a.n
+    while 3 * per_cell * m * m > budget_s and m > 256:
+        m //= 2
+    P, U0 = _oracle_problem(a, m)
+    dt = P.cfl_dt(U0, a.cfl)
+    t0 = time.perf_counter()
+    P.step_ssprk3(U0, dt)
+    el = time.perf_counter() - t0
+    return {"value": m * m * 3 / el, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"one oracle SSP-RK3 step (3 stages) of the same workload on a "
+                      f"{m}x{m} grid ({el:.1f} s wall)"}
+
+
+def main_reference(a):
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    import oracle
+    per_cell = _oracle_rate_estimate(a)
+    budget = 150.0 / max(a.steps + a.warmup, 1)  # seconds per step
+    m = a.n
+    while 3 * per_cell * m * m > budget and m > 128:
+        m //= 2
+    P, U0 = _oracle_problem(a, m)
+    U = U0.copy()
+    dt = P.cfl_dt(U0, a.cfl)
+    for _ in range(a.warmup):
+        U = P.step_ssprk3(U, dt)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        U = P.step_ssprk3(U, dt)
+    el = time.perf_counter() - t0
+    value = m * m * 3 * a.steps / el
+    cores = oracle.num_threads()
+    sample = (f"each step: one oracle SSP-RK3 step of the workload on a {m}x{m} grid "
+              f"(full size {a.n}x{a.n}); fixed dt")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": el * 1e3 / a.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(a),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)

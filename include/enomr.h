@@ -1,0 +1,178 @@
+/*
+ * enomr.h -- C ABI of libenomr.so, a GB300 (sm_103a) FP64 implementation of
+ * the ENO-MR semi-discrete right-hand side and its SSP-RK3 stage update.
+ *
+ * Method: "An efficient class of increasingly high-order ENO schemes with
+ * multi-resolution" (arXiv 2311.15504).
+ *
+ * Conventions shared by every entry point
+ * --------------------------------------
+ * Memory.   Every array argument is a DEVICE pointer on the current CUDA
+ *           device unless its description says "host".  The caller owns all
+ *           state, output and selection buffers; the library owns only the
+ *           scratch it allocates in enomr_init() and frees in enomr_free().
+ *           No entry point allocates device memory after enomr_init().
+ * Layout.   FP64, component-major ("structure of arrays"), x fastest:
+ *             scalar advection   U[nx]
+ *             1D Euler           U[3][nx]       (rho, rho u, rho e)
+ *             2D Euler           U[4][ny][nx]   (rho, rho u, rho v, rho e)
+ *           Pointers must be 8-byte aligned; arrays are dense (pitch = nx).
+ * Streams.  All work is enqueued on the stream given to enomr_init() (or
+ *           enomr_set_stream()); calls return without synchronising unless
+ *           stated.  Entry points that do not synchronise can be recorded
+ *           into a CUDA graph by the caller.
+ * Errors.   Argument errors are detected on the host and returned at once
+ *           (ENOMR_EINVAL); nothing is launched then.  CUDA launch/runtime
+ *           errors give ENOMR_ECUDA.  Non-physical states met on the device
+ *           (rho <= 0, p <= 0, Roe c^2 <= 0, NaN/Inf) set a device status
+ *           word that enomr_get_status() reads; the kernels never trap,
+ *           abort or print.
+ * Grid.     Uniform spacing dx (dy).  Boundary: periodic (requires
+ *           nx, ny >= 2g, g = (order+1)/2) or transmissive (zeroth-order
+ *           extrapolation into g ghost cells).
+ */
+#ifndef ENOMR_H
+#define ENOMR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ENOMR_API __attribute__((visibility("default")))
+#else
+#define ENOMR_API
+#endif
+
+typedef enum {
+    ENOMR_OK = 0,
+    ENOMR_EINVAL = 1,   /* bad argument; nothing was launched              */
+    ENOMR_ENOMEM = 2,   /* scratch allocation failed in enomr_init          */
+    ENOMR_ECUDA = 3,    /* a CUDA runtime call or launch failed             */
+    ENOMR_ENONPHYS = 4, /* a kernel met a non-physical state (status word)  */
+    ENOMR_ETIMEOUT = 5  /* reserved: a bounded device wait gave up          */
+} enomr_status;
+
+typedef enum { ENOMR_ADVECTION = 0, ENOMR_EULER = 1 } enomr_eq;
+typedef enum { ENOMR_PERIODIC = 0, ENOMR_TRANSMISSIVE = 1 } enomr_bc;
+
+typedef struct enomr_ctx enomr_ctx;
+
+/*
+ * enomr_init -- create a solver context for one problem.
+ *   eq         ENOMR_ADVECTION (f(u) = adv_speed * u, ndim must be 1) or
+ *              ENOMR_EULER (ideal gas, gamma > 1; ndim 1 or 2).
+ *   nx, ny     cells per direction (ny = 1 for ndim = 1).
+ *   dx, dy     spacing h of Sec. 2.1 (dy ignored in 1D).
+ *   order      R = 2r-1 in {5,7,9,11,13,15,17}: the (2r-1)-point ENO-MR scheme
+ *              (Sec. 3.1, Eq. Candidates, candidates with m,n <= r-1).
+ *   bc         ENOMR_PERIODIC or ENOMR_TRANSMISSIVE.
+ *   stream     cudaStream_t (NULL = legacy default stream).
+ * Allocates the context's device scratch (per-line alpha, status word,
+ * CFL reduction, two stage buffers and, in 2D, one partial-RHS buffer).
+ * On success *out receives the context; release it with enomr_free().
+ */
+ENOMR_API enomr_status enomr_init(enomr_ctx **out, int eq, int ndim, int64_t nx, int64_t ny,
+                                  double dx, double dy, int order, double gamma, int bc,
+                                  double adv_speed, void *stream);
+
+/* enomr_free -- release the context and its scratch (NULL is ignored). */
+ENOMR_API void enomr_free(enomr_ctx *ctx);
+
+/* enomr_strerror -- static description of a status code. */
+ENOMR_API const char *enomr_strerror(int status);
+
+/* enomr_set_stream -- change the stream later calls are enqueued on. */
+ENOMR_API enomr_status enomr_set_stream(enomr_ctx *ctx, void *stream);
+
+/*
+ * enomr_rhs -- dUdt = L(U), Eq. (1DWENOFD):
+ *   L(U)_i = -(F_{i+1/2} - F_{i-1/2})/dx [ - (G_{j+1/2} - G_{j-1/2})/dy in 2D ],
+ * with F from the global Lax-Friedrichs split (Eq. LF_Flux_Split; for
+ * Euler per characteristic field k, alpha_k = max |lambda_k| over the
+ * cells of the line), Roe-averaged characteristic projection (Sec. 4),
+ * ENO-MR selection (Sec. 3.2 Steps 1-3) and reconstruction
+ * (Eq. ReconstructedFlux) on each side, and back-projection.
+ * U and dUdt: device, layout above, must not overlap.
+ */
+ENOMR_API enomr_status enomr_rhs(enomr_ctx *ctx, const double *U, double *dUdt);
+
+/*
+ * enomr_stage -- one stage s in {1,2,3} of SSP-RK3 (Eq. TVD3rdRK):
+ *   s=1: Uout = Un + dt L(Un)                     (Us must equal Un)
+ *   s=2: Uout = 3/4 Un + 1/4 (Us + dt L(Us))
+ *   s=3: Uout = 1/3 Un + 2/3 (Us + dt L(Us))
+ * The RHS is fused with the combination.  dt > 0 (host value).  Uout may
+ * alias Un but not Us.
+ */
+ENOMR_API enomr_status enomr_stage(enomr_ctx *ctx, int stage, const double *Un, const double *Us,
+                                   double *Uout, double dt);
+
+/*
+ * enomr_step -- one full SSP-RK3 step in place on U (device).
+ *   dt > 0: use dt.  dt <= 0: dt = cfl-based step computed on the device
+ *   from U^n (1D: cfl*dx/max(|u|+c); 2D: cfl/max((|u|+c)/dx+(|v|+c)/dy);
+ *   advection: cfl*dx/|a|).
+ *   dt_used (host, may be NULL): if non-NULL the call synchronises the
+ *   stream and stores the dt that was used.
+ * Uses the context's two stage buffers; the call is not re-entrant on one
+ * context.
+ */
+ENOMR_API enomr_status enomr_step(enomr_ctx *ctx, double *U, double dt, double cfl,
+                                  double *dt_used);
+
+/* enomr_cfl_dt -- the CFL step of enomr_step for state U, returned in
+ * *dt_host (host).  Synchronises the stream. */
+ENOMR_API enomr_status enomr_cfl_dt(enomr_ctx *ctx, const double *U, double cfl, double *dt_host);
+
+/*
+ * enomr_debug_selection -- the stencil chosen at every interface, field and
+ * side for state U (same arithmetic as enomr_rhs).  sel (device, uint8):
+ *   advection  [2][nx+1]
+ *   1D Euler   [2][3][nx+1]
+ *   2D Euler   x sweep [2][4][ny][nx+1] followed by y sweep [2][4][nx][ny+1]
+ * side 0 = f^+, 1 = f^-; interface k is x_{k-1/2} (between cells k-1, k).
+ * Field order: (u-c, u, [shear], u+c) in the sweep's normal velocity.
+ * Value: t in [0,T) = t-th tested candidate of Eq. (Candidates) (filtered to
+ * the order), T, T+1, T+2 = minmod outcome S(0,1), S(1,0), S(0,0)
+ * (Step 3.2).  T = 4,7,10,14,18,22,26 for orders 5..17.
+ */
+ENOMR_API enomr_status enomr_debug_selection(enomr_ctx *ctx, const double *U, uint8_t *sel);
+
+/* enomr_get_status -- synchronise the stream, read and clear the device
+ * status word: ENOMR_OK or ENOMR_ENONPHYS. */
+ENOMR_API enomr_status enomr_get_status(enomr_ctx *ctx);
+
+/*
+ * Measurement hooks (not part of the method).
+ * enomr_profile_begin -- record CUDA events around the next max_launches
+ *   launches of one kernel of this context: 1 = the x sweep (1D: the sweep,
+ *   advection: the advection kernel), 2 = the y sweep (2D), 3 = the per-line
+ *   alpha reduction, 0 = stop.  Creates the events (host call, not for use
+ *   inside stream capture).
+ * enomr_profile_end -- synchronise the stream and return how many launches
+ *   were timed and their summed device time in milliseconds.
+ */
+ENOMR_API enomr_status enomr_profile_begin(enomr_ctx *ctx, int kernel, int max_launches);
+ENOMR_API enomr_status enomr_profile_end(enomr_ctx *ctx, int *n_launches, double *total_ms);
+
+/*
+ * enomr_probe_fp64_fma -- FP64 FMA throughput of the current device: a
+ * kernel of eight independent fma chains per thread (8 CTAs of 256 threads
+ * per SM) runs iters iterations once to warm up and once timed on stream.
+ * Returns the timed seconds and the flops it performed (2 per fma).
+ * sink: device scratch of at least 8 * SM-count doubles (never written in
+ * practice).  Synchronises the stream.
+ */
+ENOMR_API enomr_status enomr_probe_fp64_fma(void *stream, int64_t iters, double *sink,
+                                            double *seconds, double *flops);
+
+/* enomr_num_tested -- T for an order (see above), or -1. */
+ENOMR_API int enomr_num_tested(int order);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ENOMR_H */

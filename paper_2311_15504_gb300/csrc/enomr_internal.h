@@ -1,0 +1,69 @@
+// enomr_internal.h -- launch arguments shared by the API translation unit and
+// the per-order kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace enomr {
+
+// Status bits of the device status word.
+enum : int { ST_NONPHYS_CELL = 1, ST_NONPHYS_ROE = 2 };
+
+// What a sweep does with its flux difference D_i = -(F_{i+1/2}-F_{i-1/2})/h.
+enum EpiMode : int {
+    EPI_STORE = 0,   // out = D (+ Dprev)
+    EPI_STAGE = 1    // out = c0*Un + c1*(Us + dt*(D (+ Dprev)))
+};
+
+struct Epilogue {
+    int mode;
+    double c0, c1;
+    const double *dt_dev;  // device scalar dt (EPI_STAGE)
+    const double *Un;      // U^n, same layout as the state (EPI_STAGE)
+    const double *Dprev;   // partial RHS of an earlier sweep, or nullptr
+    double *out;
+};
+
+// One 1D line sweep of the Euler equations (1D: C = 3; 2D x or y sweep: C = 4).
+struct SweepArgs {
+    const double *U;       // stage state, [C][ny][nx]
+    long long nx, ny;
+    int bc;                // 0 periodic, 1 transmissive
+    double gm1, inv_gm1, gamma;
+    double inv_h;
+    const double *alpha;   // [lines][3]: max|un-c|, max|un|, max|un+c|
+    uint8_t *sel;          // optional selection dump for this sweep
+    int *status;
+    Epilogue epi;
+};
+
+struct AdvArgs {
+    const double *U;       // [nx]
+    long long n;
+    int bc;
+    double a, inv_h;
+    uint8_t *sel;          // optional [2][n+1]
+    Epilogue epi;
+};
+
+struct AlphaArgs {
+    const double *U;
+    long long nx, ny;
+    double gm1, gamma, inv_dx, inv_dy;
+    double *ax;            // [ny][3], zeroed before the launch
+    double *ay;            // [nx][3] (2D only), zeroed before the launch
+    double *smax;          // CFL wave-speed max (may be nullptr)
+    int *status;
+};
+
+template <int R> cudaError_t launch_advection(const AdvArgs &a, cudaStream_t s);
+template <int R> cudaError_t launch_euler1d(const SweepArgs &a, cudaStream_t s);
+template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, cudaStream_t s);
+template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, cudaStream_t s);
+
+cudaError_t launch_alpha(int C, const AlphaArgs &a, cudaStream_t s);
+cudaError_t launch_set_dt(const double *smax, double cfl, double dt_fixed, double *dt_dev,
+                          cudaStream_t s);
+
+}  // namespace enomr

@@ -1,0 +1,394 @@
+// enomr_kernels.cuh -- FP64 CUDA kernels for the ENO-MR right-hand side.
+//
+// arXiv 2311.15504: Sec. 2.1 (Eq. 1DWENOFD, Eq. LF_Flux_Split), Sec. 3.1
+// (Eq. Candidates), Sec. 3.2 (Steps 1-3), Sec. 4 (Roe-averaged
+// characteristic decomposition, Euler equations), Eq. TVD3rdRK.
+//
+// Design (GB300): the path is bound by the FP64 pipe, not by HBM, so the
+// kernels minimise FP64 instructions:
+//  * |x|, max, min and every IS < IS_0 test run on the integer ALU: for
+//    non-negative doubles the IEEE bit pattern orders like an int64.
+//  * the baseline indicator uses fma(-2, v_{-1}, v_0) + v_{-2}, which rounds
+//    exactly like the written (v_0 - 2 v_{-1}) + v_{-2};
+//  * the walk over candidates is unrolled at compile time (coefficients are
+//    constant-bank operands) and warp-uniform: a lane that found its
+//    stencil is predicated off, and the warp leaves the walk as soon as no
+//    lane is still searching;
+//  * the reconstruction on the chosen stencil is one dot product over the
+//    window with a row of a shared-memory coefficient table (constant
+//    operands when the whole warp took the top stencil), the minmod
+//    fallback is a single fma;
+//  * Euler: rows of L are scaled to carry a unit entry (the scheme is
+//    invariant to such scalings, Sec. 3.3), so a projection costs 3 FMAs
+//    (1 for the shear field) instead of 4; the 1/2 of the splitting and the
+//    row scalings are folded into the back-projection.
+// Tiles: a CTA stages TP + 2g - 1 cells of NL lines (with their ghost cells,
+// wrapped or clamped) into shared memory together with primitive values
+// and physical fluxes, computes TP interface fluxes per line (one per
+// thread) and updates the TP - 1 cells between them; neighbouring tiles
+// overlap by one interface.
+#pragma once
+
+#include <stdint.h>
+
+#include "enomr_coeffs.h"
+#include "enomr_internal.h"
+
+namespace enomr {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ long long abits(double x)
+{
+    return __double_as_longlong(x) & 0x7fffffffffffffffLL;
+}
+
+__device__ __forceinline__ long long imax64(long long a, long long b) { return a > b ? a : b; }
+__device__ __forceinline__ long long imin64(long long a, long long b) { return a < b ? a : b; }
+
+__device__ __forceinline__ long long ghost(long long i, long long n, int bc)
+{
+    if (bc == 0) {
+        long long r = i % n;
+        return r < 0 ? r + n : r;
+    }
+    return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3.2 Steps 2-3.1: walk the tested candidates in printed order; the
+// first with IS = |sum b_l v_l| < IS_0 wins.
+// ---------------------------------------------------------------------------
+template <int R, int t>
+__device__ __forceinline__ void walk(const double *v, long long is0, int &sel, bool &active)
+{
+    if constexpr (t < Tab<R>::T) {
+        constexpr int g = (R + 1) / 2, W = 2 * g - 1;
+        constexpr int m = Cand<R, t>::m, n = Cand<R, t>::n;
+        if (active) {
+            double s = Coef<R>::b(t * W + g - 1 - m) * v[g - 1 - m];
+#pragma unroll
+            for (int l = -m + 1; l <= n; ++l) s = fma(Coef<R>::b(t * W + g - 1 + l), v[g - 1 + l], s);
+            if (abits(s) < is0) {
+                sel = t;
+                active = false;
+            }
+        }
+        if (__any_sync(FULL, active)) walk<R, t + 1>(v, is0, sel, active);
+    }
+}
+
+// ENO-MR value of one window v[0..W-1] (v[g-1] = f_j).  All 32 lanes must
+// call it together; lanes with valid == false take part in the warp votes
+// only.  sA: shared copy of the a_l table of order R.
+template <int R>
+__device__ __forceinline__ double mr_value(const double *v, const double *sA, bool valid, int &sel)
+{
+    constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T, c = g - 1;
+    // Step 1, Eq. (Baseline_IS)
+    const double d1L = v[c] - v[c - 1];
+    const double d2L = fma(-2.0, v[c - 1], v[c]) + v[c - 2];
+    const double d1R = v[c] - v[c + 1];
+    const double d2R = fma(-2.0, v[c + 1], v[c]) + v[c + 2];
+    const long long is0 = imin64(imax64(abits(d1L), abits(d2L)), imax64(abits(d1R), abits(d2R)));
+    // IS >= 0 always, so with IS_0 = 0 no candidate can pass: skip the walk
+    // (same outcome as testing every candidate).
+    bool active = valid && is0 != 0;
+    sel = T;
+    walk<R, 0>(v, is0, sel, active);
+    active = active || (valid && is0 == 0);
+    // Step 3.2: minmod(a, b), a = f_{j+1} - f_j = -d1R, b = f_j - f_{j-1} = d1L
+    double mm = 0.0;
+    if (active || !valid) {
+        const long long ba = __double_as_longlong(d1R), bb = __double_as_longlong(d1L);
+        const bool nz = abits(d1R) != 0 && abits(d1L) != 0;
+        const bool same = nz && ((ba ^ bb) < 0);  // a = -d1R: signs of a, b agree
+        if (!same) {
+            sel = T + 2;
+        } else if (abits(d1R) <= abits(d1L)) {
+            sel = T;
+            mm = -d1R;
+        } else {
+            sel = T + 1;
+            mm = d1L;
+        }
+    }
+    double val;
+    if (__all_sync(FULL, sel == 0)) {
+        val = Coef<R>::a(0) * v[0];
+#pragma unroll
+        for (int l = 1; l < W; ++l) val = fma(Coef<R>::a(l), v[l], val);
+    } else if (sel < T) {
+        const double *row = sA + sel * W;
+        val = 0.0;
+#pragma unroll
+        for (int l = 0; l < W; ++l) val = fma(row[l], v[l], val);
+    } else {
+        val = fma(0.5, mm, v[c]);
+    }
+    return val;
+}
+
+template <int R>
+__device__ __forceinline__ void load_a_table(double *sA, int tid, int nthreads)
+{
+    constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
+    for (int i = tid; i < T * W; i += nthreads) sA[i] = Coef<R>::a_table()[i];
+}
+
+// ---------------------------------------------------------------------------
+// Epilogue: D -> output
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void epilogue(const Epilogue &e, long long idx, double D, double Us)
+{
+    if (e.Dprev) D = e.Dprev[idx] + D;
+    if (e.mode == EPI_STORE) {
+        e.out[idx] = D;
+    } else {
+        const double dt = *e.dt_dev;
+        e.out[idx] = e.c0 * e.Un[idx] + e.c1 * fma(dt, D, Us);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Scalar advection f(u) = a u, alpha = |a|: f^+ = a u, f^- = 0 for a >= 0
+// (mirror for a < 0).  One thread per interface.
+// ---------------------------------------------------------------------------
+template <int R, int TP>
+__global__ void __launch_bounds__(TP) k_advection(AdvArgs A)
+{
+    constexpr int g = (R + 1) / 2, W = 2 * g - 1, S = TP + 2 * g - 1, T = Tab<R>::T;
+    __shared__ double sf[S];
+    __shared__ double sFh[TP];
+    __shared__ double sA[T * W];
+    const int p = threadIdx.x;
+    const long long x0 = (long long)blockIdx.x * (TP - 1);
+    load_a_table<R>(sA, p, TP);
+    for (int s = p; s < S; s += TP) sf[s] = A.a * A.U[ghost(x0 - g + s, A.n, A.bc)];
+    __syncthreads();
+    const long long k = x0 + p;  // interface x_{k-1/2}
+    const bool valid = k <= A.n;
+    double v[W];
+    if (A.a >= 0.0) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) v[j] = sf[p + j];           // f^+ at cell k-1+l
+    } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) v[j] = sf[p + 2 * g - 1 - j];  // f^- at cell k-l
+    }
+    int sel;
+    const double fh = mr_value<R>(v, sA, valid, sel);
+    sFh[p] = fh;
+    if (A.sel && valid) {
+        const long long NI = A.n + 1;
+        A.sel[(A.a >= 0.0 ? 0 : NI) + k] = (uint8_t)sel;
+        A.sel[(A.a >= 0.0 ? NI : 0) + k] = (uint8_t)(T + 2);
+    }
+    __syncthreads();
+    if (p < TP - 1) {
+        const long long i = x0 + p;
+        if (i < A.n) {
+            const double D = -(sFh[p + 1] - sFh[p]) * A.inv_h;
+            epilogue(A.epi, i, D, A.U[i]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Euler line sweep.  DIR 0: lines are rows (x contiguous); DIR 1: lines are
+// columns.  C = 3 (1D) or 4 (2D, components rho, m_x, m_y, E).
+// ---------------------------------------------------------------------------
+template <int R, int C, int DIR, int TP, int NL>
+__global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
+{
+    constexpr int g = (R + 1) / 2, W = 2 * g - 1, S = TP + 2 * g - 1, T = Tab<R>::T;
+    constexpr int NT = TP * NL;
+    constexpr int QN = (DIR == 0) ? 1 : 2;  // normal momentum component
+    constexpr int QT = (DIR == 0) ? 2 : 1;  // tangential momentum component (C = 4)
+    __shared__ double sU[C][NL][S];
+    __shared__ double sF[C][NL][S];
+    __shared__ double sP[4][NL][S];  // sqrt(rho), u_n, u_t, H
+    __shared__ double sFh[C][NL][TP];
+    __shared__ double sA[T * W];
+
+    const long long nx = A.nx, ny = A.ny, ncell = nx * ny;
+    const long long nlen = (DIR == 0) ? nx : ny;
+    const long long nlines = (DIR == 0) ? ny : nx;
+    const long long x0 = (long long)((DIR == 0) ? blockIdx.x : blockIdx.y) * (TP - 1);
+    const long long l0 = (long long)((DIR == 0) ? blockIdx.y : blockIdx.x) * NL;
+    const int tid = threadIdx.x;
+    load_a_table<R>(sA, tid, NT);
+
+    // ---- stage cells, primitives and physical fluxes (normal direction)
+    for (int idx = tid; idx < NL * S; idx += NT) {
+        int line, s;
+        if (DIR == 0) {
+            line = idx / S;
+            s = idx - line * S;
+        } else {
+            s = idx / NL;
+            line = idx - s * NL;
+        }
+        long long L = l0 + line;
+        if (L >= nlines) L = nlines - 1;
+        const long long cell = ghost(x0 - g + s, nlen, A.bc);
+        const long long gi = (DIR == 0) ? L * nx + cell : cell * nx + L;
+        double u[C];
+#pragma unroll
+        for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
+        const double rho = u[0];
+        const double ir = 1.0 / rho;
+        const double un = u[QN] * ir;
+        const double ut = (C == 4) ? u[QT] * ir : 0.0;
+        const double E = u[C - 1];
+        const double p = A.gm1 * (E - 0.5 * rho * (un * un + ut * ut));
+        if (!(rho > 0.0) || !(p > 0.0) || !(fabs(E) < 1e300)) atomicOr(A.status, ST_NONPHYS_CELL);
+        sU[0][line][s] = u[0];
+        sU[1][line][s] = u[QN];
+        if (C == 4) sU[2][line][s] = u[QT];
+        sU[C - 1][line][s] = E;
+        sF[0][line][s] = u[QN];
+        sF[1][line][s] = fma(u[QN], un, p);
+        if (C == 4) sF[2][line][s] = u[QT] * un;
+        sF[C - 1][line][s] = (E + p) * un;
+        sP[0][line][s] = sqrt(rho);
+        sP[1][line][s] = un;
+        sP[2][line][s] = ut;
+        sP[3][line][s] = (E + p) * ir;
+    }
+    __syncthreads();
+
+    // ---- one interface per thread
+    int p, line;
+    if (DIR == 0) {
+        p = tid % TP;
+        line = tid / TP;
+    } else {
+        line = tid % NL;
+        p = tid / NL;
+    }
+    const long long Lg = l0 + line;
+    const long long k = x0 + p;  // interface x_{k-1/2}, cells k-1 | k
+    const bool valid = (Lg < nlines) && (k <= nlen);
+    const int sl = p + g - 1, sr = p + g;
+
+    // Roe average (Sec. 4)
+    const double qL = sP[0][line][sl], qR = sP[0][line][sr];
+    const double rs = 1.0 / (qL + qR);
+    const double uh = (qL * sP[1][line][sl] + qR * sP[1][line][sr]) * rs;
+    const double vh = (C == 4) ? (qL * sP[2][line][sl] + qR * sP[2][line][sr]) * rs : 0.0;
+    const double Hh = (qL * sP[3][line][sl] + qR * sP[3][line][sr]) * rs;
+    const double hq = 0.5 * (uh * uh + vh * vh);
+    const double c2 = A.gm1 * (Hh - hq);
+    if (valid && !(c2 > 0.0)) atomicOr(A.status, ST_NONPHYS_ROE);
+    const double cs = sqrt(c2);
+    const double kap = cs * A.inv_gm1;   // c / (gamma-1)
+    const double c2g = c2 * A.inv_gm1;   // c^2 / (gamma-1)
+    const double b1 = A.gm1 / c2;        // (gamma-1) / c^2
+
+    const double *al = A.alpha + 3 * (Lg < nlines ? Lg : nlines - 1);
+    const double a_m = al[0], a_0 = al[1], a_p = al[2];
+
+    // Back-projection accumulators.  With phi_f = s_f (f^+ + f^-)_f and the
+    // inverse row scalings s = (b1/4, -b1/2, [1/2,] b1/4) (the 1/2 of the
+    // splitting included), F = R phi reads
+    //   F0 = (phi_0 + phi_a) + phi_1,   F1 = u F0 + c (phi_a - phi_0),
+    //   F2 = v F0 + phi_2 (2D),         FE = H (phi_0 + phi_a) + u c (phi_a - phi_0)
+    //                                        + hq phi_1 + v phi_2,
+    // phi_a being the u+c field.
+    double acc_s = 0.0, acc_d = 0.0, ph1 = 0.0, ph2 = 0.0;
+#pragma unroll 1
+    for (int f = 0; f < C; ++f) {
+        // scaled left-eigenvector row with a unit entry
+        const bool shear = (C == 4 && f == 2);
+        double l0c, l1c, alpha;
+        if (shear) {
+            l0c = -vh;
+            l1c = 0.0;
+            alpha = a_0;
+        } else if (f == 0) {
+            l0c = fma(uh, kap, hq);
+            l1c = -(uh + kap);
+            alpha = a_m;
+        } else if (f == C - 1) {
+            l0c = fma(-uh, kap, hq);
+            l1c = -(uh - kap);
+            alpha = a_p;
+        } else {
+            l0c = hq - c2g;
+            l1c = -uh;
+            alpha = a_0;
+        }
+        double vp[W], vm[W];
+#pragma unroll
+        for (int j = 0; j < 2 * g; ++j) {
+            const int s = p + j;
+            double w, q;
+            if (shear) {
+                w = fma(l0c, sU[0][line][s], sU[2][line][s]);
+                q = fma(l0c, sF[0][line][s], sF[2][line][s]);
+            } else {
+                w = sU[C - 1][line][s];
+                q = sF[C - 1][line][s];
+                if (C == 4) {
+                    w = fma(-vh, sU[2][line][s], w);
+                    q = fma(-vh, sF[2][line][s], q);
+                }
+                w = fma(l1c, sU[1][line][s], w);
+                q = fma(l1c, sF[1][line][s], q);
+                w = fma(l0c, sU[0][line][s], w);
+                q = fma(l0c, sF[0][line][s], q);
+            }
+            if (j <= 2 * g - 2) vp[j] = fma(alpha, w, q);           // cell k-1+l, l = j-(g-1)
+            if (j >= 1) vm[2 * g - 1 - j] = fma(-alpha, w, q);      // cell k-l,   l = g-j
+        }
+        int selp, selm;
+        const double fp = mr_value<R>(vp, sA, valid, selp);
+        const double fm = mr_value<R>(vm, sA, valid, selm);
+        const double ft = fp + fm;
+        if (f == 0) {
+            const double ph = 0.25 * b1 * ft;
+            acc_s += ph;
+            acc_d -= ph;
+        } else if (f == C - 1) {
+            const double ph = 0.25 * b1 * ft;
+            acc_s += ph;
+            acc_d += ph;
+        } else if (shear) {
+            ph2 = 0.5 * ft;
+        } else {
+            ph1 = -0.5 * b1 * ft;
+        }
+        if (A.sel && valid) {
+            const long long NI = nlen + 1;
+            A.sel[((0 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selp;
+            A.sel[((1 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selm;
+        }
+    }
+    double Fh[C];
+    Fh[0] = acc_s + ph1;
+    Fh[1] = fma(uh, Fh[0], cs * acc_d);
+    if (C == 4) Fh[2] = fma(vh, Fh[0], ph2);
+    Fh[C - 1] = fma(Hh, acc_s, fma(uh * cs, acc_d, fma(hq, ph1, vh * ph2)));
+#pragma unroll
+    for (int q = 0; q < C; ++q) sFh[q][line][p] = Fh[q];
+    __syncthreads();
+
+    // ---- flux difference and epilogue for the TP-1 cells of the tile
+    if (p < TP - 1 && Lg < nlines) {
+        const long long i = x0 + p;
+        if (i < nlen) {
+            const long long gi = (DIR == 0) ? Lg * nx + i : i * nx + Lg;
+            const int sc = p + g;  // staged index of cell i
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+                // map line component back to the state component
+                const int qs = (q == 1) ? QN : ((C == 4 && q == 2) ? QT : q);
+                const double D = -(sFh[q][line][p + 1] - sFh[q][line][p]) * A.inv_h;
+                epilogue(A.epi, qs * ncell + gi, D, sU[q][line][sc]);
+            }
+        }
+    }
+}
+
+}  // namespace enomr

@@ -1,0 +1,51 @@
+// enomr_orders.cuh -- launchers of the per-order kernels.  Each
+// enomr_o<R>.cu defines ENOMR_R and includes this file, so the seven orders
+// compile as separate translation units in parallel.
+#pragma once
+
+#include "enomr_kernels.cuh"
+
+namespace enomr {
+
+// Tile shapes (interfaces per line x lines per CTA).
+constexpr int ADV_TP = 256;
+constexpr int E1_TP = 64;
+constexpr int X_TP = 128, X_NL = 2;
+constexpr int Y_TP = 64, Y_NL = 4;
+
+template <int R> cudaError_t launch_advection(const AdvArgs &a, cudaStream_t s)
+{
+    const long long tiles = (a.n + ADV_TP - 2) / (ADV_TP - 1);
+    k_advection<R, ADV_TP><<<(unsigned)tiles, ADV_TP, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t launch_euler1d(const SweepArgs &a, cudaStream_t s)
+{
+    const long long tiles = (a.nx + E1_TP - 2) / (E1_TP - 1);
+    k_sweep<R, 3, 0, E1_TP, 1><<<dim3((unsigned)tiles, 1), E1_TP, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, cudaStream_t s)
+{
+    const long long tx = (a.nx + X_TP - 2) / (X_TP - 1);
+    const long long ty = (a.ny + X_NL - 1) / X_NL;
+    k_sweep<R, 4, 0, X_TP, X_NL><<<dim3((unsigned)tx, (unsigned)ty), X_TP * X_NL, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, cudaStream_t s)
+{
+    const long long tx = (a.nx + Y_NL - 1) / Y_NL;
+    const long long ty = (a.ny + Y_TP - 2) / (Y_TP - 1);
+    k_sweep<R, 4, 1, Y_TP, Y_NL><<<dim3((unsigned)tx, (unsigned)ty), Y_TP * Y_NL, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_advection<ENOMR_R>(const AdvArgs &, cudaStream_t);
+template cudaError_t launch_euler1d<ENOMR_R>(const SweepArgs &, cudaStream_t);
+template cudaError_t launch_euler2d_x<ENOMR_R>(const SweepArgs &, cudaStream_t);
+template cudaError_t launch_euler2d_y<ENOMR_R>(const SweepArgs &, cudaStream_t);
+
+}  // namespace enomr

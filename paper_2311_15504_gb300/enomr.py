@@ -1,0 +1,196 @@
+"""Thin Python binding of libenomr.so (argument marshalling only).
+
+Every computation runs in the CUDA kernels of the library; this module only
+checks tensors, passes device pointers and the current torch stream, and
+turns status codes into exceptions.  There is no CPU fallback: importing this
+module fails if the compiled library is missing.
+
+C ABI: include/enomr.h.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+ADVECTION, EULER = 0, 1
+PERIODIC, TRANSMISSIVE = 0, 1
+ORDERS = (5, 7, 9, 11, 13, 15, 17)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libenomr.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() first "
+                      "(the ENO-MR path has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+_SIGS = {
+    "enomr_init": (_I, [ctypes.POINTER(_P), _I, _I, _L, _L, _D, _D, _I, _D, _I, _D, _P]),
+    "enomr_free": (None, [_P]),
+    "enomr_strerror": (ctypes.c_char_p, [_I]),
+    "enomr_set_stream": (_I, [_P, _P]),
+    "enomr_rhs": (_I, [_P, _P, _P]),
+    "enomr_stage": (_I, [_P, _I, _P, _P, _P, _D]),
+    "enomr_step": (_I, [_P, _P, _D, _D, _P]),
+    "enomr_cfl_dt": (_I, [_P, _P, _D, _P]),
+    "enomr_debug_selection": (_I, [_P, _P, _P]),
+    "enomr_get_status": (_I, [_P]),
+    "enomr_num_tested": (_I, [_I]),
+    "enomr_profile_begin": (_I, [_P, _I, _I]),
+    "enomr_profile_end": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "enomr_probe_fp64_fma": (_I, [_P, ctypes.c_int64, _P, ctypes.POINTER(_D),
+                                 ctypes.POINTER(_D)]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class EnomrError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {_lib.enomr_strerror(code).decode()} (status {code})")
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise EnomrError(code, where)
+
+
+def num_tested(order: int) -> int:
+    return _lib.enomr_num_tested(order)
+
+
+def probe_fp64_fma(iters: int = 20000, device=None):
+    """Measured FP64 FMA throughput of the device in flop/s."""
+    dev = torch.device(device if device is not None else "cuda")
+    sink = torch.zeros(8 * 1024, dtype=torch.float64, device=dev)
+    sec, fl = ctypes.c_double(), ctypes.c_double()
+    s = torch.cuda.current_stream(dev).cuda_stream
+    _check(_lib.enomr_probe_fp64_fma(_P(s), int(iters), _P(sink.data_ptr()), ctypes.byref(sec),
+                                     ctypes.byref(fl)), "enomr_probe_fp64_fma")
+    return fl.value / sec.value, sec.value
+
+
+class Solver:
+    """One ENO-MR problem on one GPU.
+
+    eq: ADVECTION (1D, f = adv_speed * u) or EULER (1D: shape = nx, state
+    [3, nx]; 2D: shape = (ny, nx), state [4, ny, nx]).  States are float64
+    CUDA tensors, contiguous.
+    """
+
+    def __init__(self, eq, shape, order=9, dx=1.0, dy=None, bc=TRANSMISSIVE, gamma=1.4,
+                 adv_speed=1.0, device=None):
+        if isinstance(shape, int):
+            ndim, ny, nx = 1, 1, shape
+        else:
+            ndim, (ny, nx) = 2, shape
+        self.eq, self.ndim, self.nx, self.ny, self.order = eq, ndim, nx, ny, order
+        self.bc = bc
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.type != "cuda":
+            raise ValueError("the ENO-MR solver runs on CUDA devices only")
+        self.ncomp = 1 if eq == ADVECTION else (4 if ndim == 2 else 3)
+        self.state_shape = ((nx,) if eq == ADVECTION else
+                            ((3, nx) if ndim == 1 else (4, ny, nx)))
+        ctx = _P()
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            _check(_lib.enomr_init(ctypes.byref(ctx), eq, ndim, nx, ny, dx,
+                                   dy if dy is not None else dx, order, gamma, bc, adv_speed,
+                                   _P(stream)), "enomr_init")
+        self._ctx = ctx
+
+    # -- helpers ----------------------------------------------------------
+    def _stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        _check(_lib.enomr_set_stream(self._ctx, _P(s)), "enomr_set_stream")
+
+    def _state(self, U, name="U"):
+        if not isinstance(U, torch.Tensor) or U.dtype != torch.float64:
+            raise TypeError(f"{name} must be a float64 tensor")
+        if U.device != self.device and not (U.device.type == "cuda" and self.device.index is None):
+            raise ValueError(f"{name} must live on {self.device}")
+        if tuple(U.shape) != self.state_shape or not U.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with shape {self.state_shape}")
+        return _P(U.data_ptr())
+
+    def n_sel(self):
+        if self.eq == ADVECTION:
+            return 2 * (self.nx + 1)
+        if self.ndim == 1:
+            return 6 * (self.nx + 1)
+        return 8 * self.ny * (self.nx + 1) + 8 * self.nx * (self.ny + 1)
+
+    # -- API --------------------------------------------------------------
+    def rhs(self, U, out=None):
+        pu = self._state(U)
+        if out is None:
+            out = torch.empty_like(U)
+        po = self._state(out, "out")
+        self._stream()
+        _check(_lib.enomr_rhs(self._ctx, pu, po), "enomr_rhs")
+        return out
+
+    def stage(self, s, Un, Us, out, dt):
+        self._stream()
+        _check(_lib.enomr_stage(self._ctx, s, self._state(Un), self._state(Us),
+                                self._state(out, "out"), float(dt)), "enomr_stage")
+        return out
+
+    def step(self, U, dt=0.0, cfl=0.5, return_dt=False):
+        pu = self._state(U)
+        self._stream()
+        if return_dt:
+            d = ctypes.c_double()
+            _check(_lib.enomr_step(self._ctx, pu, float(dt), float(cfl), ctypes.byref(d)),
+                   "enomr_step")
+            return d.value
+        _check(_lib.enomr_step(self._ctx, pu, float(dt), float(cfl), None), "enomr_step")
+        return None
+
+    def cfl_dt(self, U, cfl=0.5):
+        d = ctypes.c_double()
+        self._stream()
+        _check(_lib.enomr_cfl_dt(self._ctx, self._state(U), float(cfl), ctypes.byref(d)),
+               "enomr_cfl_dt")
+        return d.value
+
+    def selection(self, U):
+        sel = torch.empty(self.n_sel(), dtype=torch.uint8, device=self.device)
+        self._stream()
+        _check(_lib.enomr_debug_selection(self._ctx, self._state(U), _P(sel.data_ptr())),
+               "enomr_debug_selection")
+        return sel
+
+    def profile_begin(self, kernel: int, max_launches: int):
+        """Time the next launches of one kernel (1 x sweep, 2 y sweep, 3 alpha)."""
+        _check(_lib.enomr_profile_begin(self._ctx, kernel, max_launches), "enomr_profile_begin")
+
+    def profile_end(self):
+        n, ms = _I(), _D()
+        _check(_lib.enomr_profile_end(self._ctx, ctypes.byref(n), ctypes.byref(ms)),
+               "enomr_profile_end")
+        return n.value, ms.value
+
+    def check_status(self):
+        self._stream()
+        _check(_lib.enomr_get_status(self._ctx), "enomr_get_status")
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            _lib.enomr_free(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

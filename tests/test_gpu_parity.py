@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle.
+
+Selection ids must match except at near-ties (tests/parity.py); values are
+compared with the oracle re-run on the CUDA path's selection, to
+1e-12 * max(||L||_inf, ||F||_inf/h).  Sizes span several tiles and end
+with ragged tails (x tiles hold 127 cells, y tiles 63, 1D tiles 63,
+advection tiles 255).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from parity import assert_selection, assert_values, euler_flux_scale
+from paper_2311_15504_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+ORDERS = [5, 7, 9, 11, 13, 15, 17]
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build_cuda()
+    from paper_2311_15504_gb300 import enomr
+    return enomr
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+# ---------------------------------------------------------------------------
+# scalar advection
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("R", ORDERS)
+@pytest.mark.parametrize("kind", ["sine", "step", "random"])
+@pytest.mark.parametrize("N,bc", [(200, 0), (777, 0), (531, 1)])
+def test_advection_rhs(E, R, kind, N, bc):
+    if kind == "sine":
+        u, h = wl.advection_sine(N, power=4)
+    elif kind == "step":
+        u, h = wl.advection_step(N)
+    else:
+        u = np.random.Generator(np.random.PCG64(R * N)).standard_normal(N)
+        h = 2.0 / N
+    for a in (1.0, -0.75):
+        s = E.Solver(E.ADVECTION, N, order=R, dx=h, bc=bc, adv_speed=a)
+        ud = dev(u)
+        sel = s.selection(ud).cpu().numpy().reshape(2, N + 1)
+        ref = oracle.rhs_advection(u, h, R, bc=bc, a=a, want_sel=True, want_win=True)
+        assert_selection(R, sel, ref["sel"], ref["win"], f"adv R={R} {kind} a={a}")
+        forced = oracle.rhs_advection(u, h, R, bc=bc, a=a, forced=sel.reshape(-1))
+        got = s.rhs(ud).cpu().numpy()
+        assert_values(got, forced["rhs"], np.abs(a * u).max() / h, f"adv R={R} {kind}")
+        s.check_status()
+
+
+# ---------------------------------------------------------------------------
+# 1D Euler
+# ---------------------------------------------------------------------------
+def _euler1d_case(kind, N):
+    if kind == "shock_entropy":
+        return wl.shock_entropy(N)
+    if kind == "lax":
+        return wl.lax_tube(N)
+    U, h = wl.density_wave_1d(N)
+    return U, h
+
+
+@pytest.mark.parametrize("R", ORDERS)
+@pytest.mark.parametrize("kind,N,bc", [("shock_entropy", 400, 1), ("lax", 301, 1),
+                                       ("wave", 190, 0)])
+def test_euler1d_rhs(E, R, kind, N, bc):
+    U, h = _euler1d_case(kind, N)
+    s = E.Solver(E.EULER, N, order=R, dx=h, bc=bc)
+    Ud = dev(U)
+    sel = s.selection(Ud).cpu().numpy().reshape(2, 3, N + 1)
+    ref = oracle.rhs_euler1d(U, h, R, bc=bc, want_sel=True, want_win=True)
+    assert_selection(R, sel, ref["sel"], ref["win"], f"euler1d R={R} {kind}")
+    forced = oracle.rhs_euler1d(U, h, R, bc=bc, forced=sel.reshape(-1))
+    got = s.rhs(Ud).cpu().numpy()
+    assert_values(got, forced["rhs"], euler_flux_scale(U) / h, f"euler1d R={R} {kind}")
+    s.check_status()
+
+
+# ---------------------------------------------------------------------------
+# 2D Euler
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("R", ORDERS)
+@pytest.mark.parametrize("case", ["riemann", "smooth_periodic"])
+def test_euler2d_rhs(E, R, case):
+    if case == "riemann":
+        nx, ny, bc = 300, 140, 1
+        U, dx, dy = wl.riemann2d(nx, ny, seed=R)
+    else:
+        nx, ny, bc = 133, 70, 0
+        U = wl.smooth_random_euler2d(nx, ny, seed=R)
+        dx, dy = 1.0 / nx, 1.0 / ny
+    s = E.Solver(E.EULER, (ny, nx), order=R, dx=dx, dy=dy, bc=bc)
+    Ud = dev(U)
+    sel = s.selection(Ud).cpu().numpy()
+    ref = oracle.rhs_euler2d(U, dx, dy, R, bc=bc, want_sel=True, want_win=True)
+    nsx = 8 * ny * (nx + 1)
+    assert_selection(R, sel[:nsx], ref["sel_x"], ref["win_x"], f"2d-x R={R} {case}")
+    assert_selection(R, sel[nsx:], ref["sel_y"], ref["win_y"], f"2d-y R={R} {case}")
+    forced = oracle.rhs_euler2d(U, dx, dy, R, bc=bc, forced=sel)
+    got = s.rhs(Ud).cpu().numpy()
+    assert_values(got, forced["rhs"], euler_flux_scale(U) / min(dx, dy), f"2d R={R} {case}")
+    s.check_status()
+
+
+# ---------------------------------------------------------------------------
+# time integration and final states
+# ---------------------------------------------------------------------------
+def test_stage_and_step_match_oracle(E):
+    import torch
+    U, dx, dy = wl.riemann2d(130, 70, seed=5)
+    R = 9
+    s = E.Solver(E.EULER, (70, 130), order=R, dx=dx, dy=dy, bc=1)
+    P = oracle.Problem(oracle.EQ_EULER2D, R, 130, 70, dx=dx, dy=dy, bc=oracle.BC_TRANSMISSIVE)
+    dt = P.cfl_dt(U, 0.5)
+    dt_gpu = s.cfl_dt(dev(U), 0.5)
+    assert dt_gpu == pytest.approx(dt, rel=1e-14)
+    Ud = dev(U)
+    s.step(Ud, dt=dt)
+    ref = P.step_ssprk3(U, dt)
+    assert np.abs(Ud.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
+    # explicit stages equal the fused step
+    Un = dev(U)
+    U1, U2, U3 = torch.empty_like(Un), torch.empty_like(Un), torch.empty_like(Un)
+    s.stage(1, Un, Un, U1, dt)
+    s.stage(2, Un, U1, U2, dt)
+    s.stage(3, Un, U2, U3, dt)
+    assert torch.equal(U3, Ud)
+    s.check_status()
+
+
+@pytest.mark.parametrize("R", [5, 7, 9])
+def test_config1_final_states(E, R):
+    """Advection on [-1,1], N=200, SSP-RK3 CFL 0.5 to t=2: sine (smooth,
+    L1 <= 1e-10) and unit step (shock, L1 <= 1e-6)."""
+    for kind, tol in (("sine", 1e-10), ("step", 1e-6)):
+        u, h = wl.advection_sine(200) if kind == "sine" else wl.advection_step(200)
+        dt = 0.5 * h
+        n = int(round(2.0 / dt))
+        P = oracle.Problem(oracle.EQ_ADVECTION, R, 200, dx=h, bc=oracle.BC_PERIODIC)
+        s = E.Solver(E.ADVECTION, 200, order=R, dx=h, bc=E.PERIODIC)
+        ud = dev(u)
+        ref = u.copy()
+        for _ in range(n):
+            ref = P.step_ssprk3(ref, dt)
+            s.step(ud, dt=dt)
+        got = ud.cpu().numpy()
+        assert np.abs(got - ref).mean() <= tol, (kind, np.abs(got - ref).mean())
+
+
+@pytest.mark.parametrize("R", [5, 9, 13, 17])
+def test_config2_final_state(E, R):
+    """Shock/entropy-wave interaction, N=400, transmissive, CFL 0.5, t=1.8."""
+    U, h = wl.shock_entropy(400)
+    P = oracle.Problem(oracle.EQ_EULER1D, R, 400, dx=h, bc=oracle.BC_TRANSMISSIVE)
+    s = E.Solver(E.EULER, 400, order=R, dx=h, bc=E.TRANSMISSIVE)
+    Ud = dev(U)
+    ref = U.copy()
+    t = 0.0
+    while t < 1.8:
+        dt = min(P.cfl_dt(ref, 0.5), 1.8 - t)
+        ref = P.step_ssprk3(ref, dt)
+        s.step(Ud, dt=dt)
+        t += dt
+    got = Ud.cpu().numpy()
+    l1 = np.abs(got - ref).mean()
+    assert l1 <= 1e-6, l1
+    s.check_status()
+
+
+def test_nonphysical_state_sets_status(E):
+    U, h = wl.shock_entropy(200)
+    U[0, 50] = -1.0
+    s = E.Solver(E.EULER, 200, order=5, dx=h, bc=E.TRANSMISSIVE)
+    s.rhs(dev(U))
+    with pytest.raises(E.EnomrError) as ex:
+        s.check_status()
+    assert ex.value.code == 4
+    s.check_status()  # the word is cleared after reading
+
+
+def test_constant_state_and_scale_properties(E):
+    import torch
+    U = wl.conserved_2d(np.full((80, 150), 0.9), 0.4, -0.3, 1.1)
+    s = E.Solver(E.EULER, (80, 150), order=13, dx=0.01, dy=0.02, bc=E.TRANSMISSIVE)
+    assert torch.count_nonzero(s.rhs(dev(U))) == 0
+    u, h = wl.advection_step(1000)
+    a = E.Solver(E.ADVECTION, 1000, order=17, dx=h, bc=E.PERIODIC)
+    r1 = a.rhs(dev(u))
+    r2 = a.rhs(dev(u * 2.0 ** 40))
+    assert torch.equal(r2, r1 * 2.0 ** 40)
+    assert torch.equal(a.selection(dev(u)), a.selection(dev(u * 2.0 ** 40)))
