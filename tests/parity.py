@@ -23,9 +23,10 @@ def _bsum(R):
     return [float(np.abs(oracle.candidate(R, t)[3]).sum()) for t in range(oracle.num_tested(R))]
 
 
-def classify_mismatches(R, sel_gpu, sel_orc, windows):
+def classify_mismatches(R, sel_gpu, sel_orc, windows, scale_fn=None):
     """Return (n_mismatch, n_near_tie, worst) for flattened selection arrays
-    and the oracle's windows [..., 2g-1] (same leading shape)."""
+    and the oracle's windows [..., 2g-1] (same leading shape).  scale_fn(i)
+    gives the magnitude of the terms that formed window i (default max|v|)."""
     sel_gpu = np.asarray(sel_gpu).reshape(-1)
     sel_orc = np.asarray(sel_orc).reshape(-1)
     win = np.asarray(windows).reshape(sel_orc.shape[0], -1)
@@ -38,6 +39,8 @@ def classify_mismatches(R, sel_gpu, sel_orc, windows):
     for i in bad:
         w = win[i]
         vmax = float(np.abs(w).max())
+        if scale_fn is not None:
+            vmax = max(vmax, float(scale_fn(int(i))))
         is0, _, is_, _ = oracle.mr_indicators(R, w)
         k = int(min(sel_gpu[i], sel_orc[i]))
         if k < T:
@@ -54,8 +57,8 @@ def classify_mismatches(R, sel_gpu, sel_orc, windows):
     return len(bad), ties, worst
 
 
-def assert_selection(R, sel_gpu, sel_orc, windows, what=""):
-    n, ties, worst = classify_mismatches(R, sel_gpu, sel_orc, windows)
+def assert_selection(R, sel_gpu, sel_orc, windows, what="", scale_fn=None):
+    n, ties, worst = classify_mismatches(R, sel_gpu, sel_orc, windows, scale_fn)
     assert n == ties, f"{what}: {n - ties} selection mismatches that are not near-ties (worst {worst:.2e})"
     return n
 
@@ -83,3 +86,52 @@ def euler_flux_scale(U, gamma=1.4):
     return float(max(np.abs(U[1]).max(), np.abs(U[2]).max(), np.abs(U[1] * u + p).max(),
                      np.abs(U[2] * v + p).max(), np.abs((U[3] + p) * u).max(),
                      np.abs((U[3] + p) * v).max()))
+
+
+def _phys_flux(Uc, gamma):
+    c = Uc.shape[0]
+    rho, un = Uc[0], Uc[1] / Uc[0]
+    ut = Uc[2] / Uc[0] if c == 4 else 0.0
+    p = (gamma - 1) * (Uc[-1] - 0.5 * rho * (un * un + ut * ut))
+    F = [Uc[1], Uc[1] * un + p] + ([Uc[2] * un] if c == 4 else []) + [(Uc[-1] + p) * un]
+    return np.array(F)
+
+
+def euler_scale_fn(line_state, n_lines, nlen, R, bc, alpha, gamma=1.4):
+    """scale_fn for Euler selections laid out [side][field][line][nlen+1]:
+    the largest 1/2 (|L_f| |F| + alpha_f |L_f| |U|) over the window cells,
+    with L from the oracle's Roe eigen-system.  line_state(line) returns the
+    line's cells as [nlen, c] in line components (rho, m_n, [m_t], E);
+    alpha(line) the oracle's per-field alpha."""
+    g = (R + 1) // 2
+    cache = {}
+
+    def cells(line):
+        if line not in cache:
+            cache[line] = line_state(line)
+        return cache[line]
+
+    def gidx(j):
+        if bc == 0:
+            return j % nlen
+        return min(max(j, 0), nlen - 1)
+
+    def fn(i):
+        NI = nlen + 1
+        k = i % NI
+        line = (i // NI) % n_lines
+        c = cells(line).shape[1]
+        field = (i // (NI * n_lines)) % c
+        side = i // (NI * n_lines * c)
+        X = cells(line)
+        _, Lm, _ = oracle.euler_eigen(X[gidx(k - 1)], X[gidx(k)], gamma)
+        a = alpha(line)[field]
+        best = 0.0
+        for l in range(-(g - 1), g):
+            j = k - 1 + l if side == 0 else k - l
+            Uc = X[gidx(j)]
+            m = 0.5 * (np.abs(Lm[field]) @ np.abs(_phys_flux(Uc, gamma))
+                       + a * (np.abs(Lm[field]) @ np.abs(Uc)))
+            best = max(best, float(m))
+        return best
+    return fn
