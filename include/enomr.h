@@ -169,6 +169,34 @@ ENOMR_API enomr_status enomr_profile_end(enomr_ctx *ctx, int *n_launches, double
 ENOMR_API enomr_status enomr_probe_fp64_fma(void *stream, int64_t iters, double *sink,
                                             double *seconds, double *flops);
 
+/*
+ * enomr_rhs_euler2d_noalloc -- the 2D Euler right-hand side of enomr_rhs()
+ * for callers that cannot allocate device memory: host frameworks that keep
+ * the device memory for their own caching allocator, programs with a fixed
+ * device-memory budget, and latency-sensitive loops where cudaMalloc and
+ * cudaFree would synchronise the device.  It needs no context and calls no
+ * cudaMalloc, cudaFree or other allocating routine.  The paper has no
+ * counterpart; this is a service of the library.
+ *   U, dUdt   device, [4][ny][nx] (layout above); must not overlap.
+ *   nx, ny    at most ENOMR_NOALLOC_MAX_LINES each (else ENOMR_EINVAL).
+ *   dx, dy, order, gamma, bc   as in enomr_init(); stream as there.
+ * Result: dUdt equals enomr_rhs() of a context with the same parameters.
+ * Scratch: the per-line alpha maxima and a status word live in one static
+ * device array of the library (about 0.8 MB), held on every GPU that loads
+ * the library until the process exits.  The first call on a device looks up
+ * that array's device address (a host-side set-up step, done once per
+ * device), so make the first call on each device before any stream
+ * capture.  All calls share the array and it keeps the last call's
+ * contents (each call clears what must start at zero): calls that overlap
+ * on the GPU -- on different streams, or from several host threads -- race
+ * and give wrong results; serialise them.  Non-physical states are not
+ * reported by this entry point.
+ */
+#define ENOMR_NOALLOC_MAX_LINES 16384
+ENOMR_API enomr_status enomr_rhs_euler2d_noalloc(const double *U, double *dUdt, int64_t nx,
+                                                 int64_t ny, double dx, double dy, int order,
+                                                 double gamma, int bc, void *stream);
+
 /* enomr_num_tested -- T for an order (see above), or -1. */
 ENOMR_API int enomr_num_tested(int order);
 

@@ -43,6 +43,7 @@ _SIGS = {
     "enomr_profile_end": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "enomr_probe_fp64_fma": (_I, [_P, ctypes.c_int64, _P, ctypes.POINTER(_D),
                                  ctypes.POINTER(_D)]),
+    "enomr_rhs_euler2d_noalloc": (_I, [_P, _P, _L, _L, _D, _D, _I, _D, _I, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
