@@ -109,25 +109,31 @@ class ClockSampler:
 # algorithmic FP64 work of one sweep launch (counted per interface; an FMA is
 # two flops, an add, multiply, divide or square root one)
 # ---------------------------------------------------------------------------
-def sweep_flops(order, C, sel, n_interfaces):
-    """Flops of one Euler sweep: per interface the Roe average and scaled
-    eigenvectors (28), per field the projection of the 2g-cell window
-    (40 per cell for C = 4: 20 FMAs for U and F; 24 for C = 3), the split
-    (2 FMAs per window value and side), per window: baseline indicator (8),
-    the indicators of the tested candidates up to the chosen one (2|S|-1
-    each; none when IS_0 = 0), the reconstruction on the chosen stencil
-    (2|S|-1) or the minmod fma (2), and the back-projection (C == 4: 20, C == 3: 14).  sel: the
-    selection histogram counts[T+3] over all windows of the launch."""
+def sweep_flops(order, C, sel, n_interfaces, n_flat=0):
+    """Flops of one Euler sweep.  Every interface: the Roe average and scaled
+    eigenvectors (28) and the back-projection (C == 4: 20, C == 3: 14).
+    Interfaces whose two sides have flat windows (three equal cell states at
+    the side's centre: IS_0 = 0 exactly, minmod returns v(0)) add only the
+    projection of their two centre cells (40 flops per cell for C = 4, 24 for
+    C = 3: 20 or 12 FMAs for U and F) and one split FMA per field and side.
+    Other interfaces add the projection of the 2g-cell window, the split
+    (2 FMAs per window value and side) and, per window, the baseline
+    indicator (8), the indicators of the tested candidates up to the chosen
+    one (2|S|-1 each; none when IS_0 = 0), the reconstruction on the chosen
+    stencil (2|S|-1) or the minmod fma (2).  sel: selection histogram
+    counts[T+3] over all windows of the launch (flat interfaces included)."""
     import oracle  # table sizes only
     g = (order + 1) // 2
     T = oracle.num_tested(order)
     sizes = [oracle.candidate(order, t)[0] + oracle.candidate(order, t)[1] + 1 for t in range(T)]
-    proj = (40 if C == 4 else 24) * 2 * g
-    split = C * 2 * 2 * (2 * g - 1)
-    per_iface = 28 + proj + split + (20 if C == 4 else 14)
-    flops = per_iface * n_interfaces
+    cell = 40 if C == 4 else 24
+    fixed = 28 + (20 if C == 4 else 14)
+    full = fixed + cell * 2 * g + C * 2 * 2 * (2 * g - 1)
+    flat = fixed + cell * 2 + C * 2 * 2 + C
+    flops = float(n_flat) * flat + float(n_interfaces - n_flat) * full
     walk_cum = np.cumsum([2 * s - 1 for s in sizes])
-    counts = np.asarray(sel, dtype=np.float64)
+    counts = np.asarray(sel, dtype=np.float64).copy()
+    counts[T + 2] -= 2 * C * n_flat  # the flat interfaces' windows
     for t in range(T):
         flops += counts[t] * (8 + walk_cum[t] + 2 * sizes[t] - 1)
     # minmod outcomes: S(0,1) and S(1,0) come after a full walk; S(0,0) is
@@ -135,6 +141,85 @@ def sweep_flops(order, C, sel, n_interfaces):
     flops += (counts[T] + counts[T + 1]) * (8 + walk_cum[-1] + 2)
     flops += counts[T + 2] * (8 + 2)
     return float(flops)
+
+
+def flat_interfaces(U, axis):
+    """Interfaces of a transmissive 2D sweep (axis 0: x, 1: y) whose plus and
+    minus windows are flat in the sense of the kernel's shortcut."""
+    import torch
+    X = U if axis == 0 else U.transpose(1, 2)
+    Xp = torch.nn.functional.pad(X.unsqueeze(0), (3, 3, 0, 0), mode="replicate")[0]
+    eq = (Xp[..., 1:] == Xp[..., :-1]).all(dim=0)      # eq[:, j]: padded cells j, j+1
+    nI = X.shape[2] + 1
+    e = [eq[:, o:o + nI] for o in range(5)]            # e_o: cells k-3+o, k-2+o
+    flat = ((e[0] & e[1]) | (e[2] & e[3])) & ((e[3] & e[4]) | (e[1] & e[2]))
+    return int(flat.sum().item())
+
+
+def batched_gain(enomr, workloads, dev, a, nprob=4096, order=9, reps=5):
+    """4096 independent 1D Euler Riemann problems (sizes log-uniform in
+    [128, 8192]): the persistent batched step (autotuned, captured in a CUDA
+    graph) against one enomr_step per problem (the same kernels' arithmetic,
+    all 4096 captured in one CUDA graph)."""
+    import torch
+    sizes, Us, hs = workloads.riemann_batch(nprob, seed=0)
+    B = enomr.Batch(sizes, hs, order=order, bc=enomr.TRANSMISSIVE, device=dev)
+    Ub = B.pack(Us)
+    tile, grid = B.autotune(Ub, reps=2)
+    cells = int(sizes.sum())
+
+    def timed(graph):
+        graph.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    side = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(side):
+        B.step(Ub, a.cfl)
+    torch.cuda.synchronize()
+    gb = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gb):
+        B.step(Ub, a.cfl)
+    ms_b = timed(gb)
+    Up = B.pack(Us)
+    singles = [enomr.Solver(enomr.EULER, int(n), order=order, dx=float(h),
+                            bc=enomr.TRANSMISSIVE, device=dev) for n, h in zip(sizes, hs)]
+    views = [B.view(Up, p) for p in range(nprob)]
+    with torch.cuda.stream(side):
+        for sp, v in zip(singles, views):
+            sp.step(v, 0.0, a.cfl)
+    torch.cuda.synchronize()
+    gp = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gp):
+        for sp, v in zip(singles, views):
+            sp.step(v, 0.0, a.cfl)
+    ms_p = timed(gp)
+    # same arithmetic: after the same number of steps the two states agree bitwise
+    Ub2, Up2 = B.pack(Us), B.pack(Us)
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            B.step(Ub2, a.cfl)
+            for sp, p in zip(singles, range(nprob)):
+                sp.step(B.view(Up2, p), 0.0, a.cfl)
+    torch.cuda.synchronize()
+    identical = bool(torch.equal(Ub2, Up2))
+    for sp in singles:
+        sp.close()
+    B.close()
+    return {"workload": f"{nprob} 1D Euler Riemann problems, sizes log-uniform [128, 8192] "
+                        f"({cells} cells), order {order}, transmissive, CFL {a.cfl}",
+            "batched": {"value": cells * 3 / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
+                        "tile": tile, "grid": grid, "launches_per_step": 5},
+            "per_problem": {"value": cells * 3 / (ms_p * 1e-3), "unit": UNIT,
+                            "ms_per_step": ms_p, "launches_per_step": 10 * nprob},
+            "gain": ms_p / ms_b, "bitwise_identical_after_2_steps": identical}
 
 
 def main_ours(a):
@@ -183,7 +268,7 @@ def main_ours(a):
     ms_max = float(t.item())
     cells = n * n
     value = world * cells * 3 * a.steps / (ms_max * 1e-3)
-    launches_per_step = 1 + 4 + 2 * 3  # dt, 4 alpha reductions, 2 sweeps x 3 stages
+    launches_per_step = 1 + 3 + 2 * 3  # dt, 3 alpha reductions, 2 sweeps x 3 stages
 
     extras = {}
     if rank == 0 and not a.no_extras:
@@ -193,7 +278,7 @@ def main_ours(a):
         for _ in range(a.steps):
             s.step(Uy, 0.0, a.cfl)
         ny_launch, y_ms = s.profile_end()
-        s.profile_begin(3, 4 * a.steps)
+        s.profile_begin(3, 3 * a.steps)
         for _ in range(a.steps):
             s.step(Uy, 0.0, a.cfl)
         na_launch, a_ms = s.profile_end()
@@ -203,23 +288,79 @@ def main_ours(a):
         nsx = 8 * n * (n + 1)
         hx = torch.bincount(sel[:nsx].long(), minlength=T + 3).cpu().numpy()
         hy = torch.bincount(sel[nsx:].long(), minlength=T + 3).cpu().numpy()
-        fl_x = sweep_flops(R, 4, hx, n * (n + 1))
-        fl_y = sweep_flops(R, 4, hy, n * (n + 1))
-        fp64_peak, _ = enomr.probe_fp64_fma(iters=20000, device=dev)
+        fx_flat = flat_interfaces(U, 0)
+        fy_flat = flat_interfaces(U, 1)
+        fl_x = sweep_flops(R, 4, hx, n * (n + 1), fx_flat)
+        fl_y = sweep_flops(R, 4, hy, n * (n + 1), fy_flat)
+        extras["flat_interface_fraction"] = [fx_flat / (n * (n + 1)), fy_flat / (n * (n + 1))]
+        probe, _ = enomr.probe_fp64_fma(iters=20000, device=dev)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        # 2 DFMA lanes per SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+        # peak_sustained = 2 / SM / cycle), 2 flops per DFMA, at the measured SM clock
+        peak = 2.0 * 2.0 * sms * mhz * 1e6 / 1e12
         x_avg = x_ms / max(nx_launch, 1)
         y_avg = y_ms / max(ny_launch, 1)
         dom, avg, fl = ("x_sweep", x_avg, fl_x) if x_avg >= y_avg else ("y_sweep", y_avg, fl_y)
         achieved = fl / (avg * 1e-3) / 1e12
         extras["roofline"] = {
             "bound": "alu", "pipe": "fp64", "kernel": f"k_sweep<{R},4,{0 if dom == 'x_sweep' else 1}>",
-            "achieved": round(achieved, 4), "peak": round(fp64_peak / 1e12, 4),
-            "unit": "TFLOP/s", "frac": round(achieved / (fp64_peak / 1e12), 4),
-            "peak_source": "measured live: enomr_probe_fp64_fma (8 fma chains/thread, all SMs)",
+            "achieved": round(achieved, 4), "peak": round(peak, 4),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "peak_source": (f"unit counts x clock: 2 DFMA/clk/SM x 2 flop x {sms} SMs x "
+                            f"{mhz:.0f} MHz (median SM clock of the timed region)"),
+            "peak_probe_tflops": round(probe / 1e12, 4),
             "traffic": None,
             "avg_launch_ms": round(avg, 4), "algorithmic_flops_per_launch": fl,
             "x_sweep_ms": round(x_avg, 4), "y_sweep_ms": round(y_avg, 4),
             "alpha_ms": round(a_ms / max(na_launch, 1), 4)}
         extras["selection_histogram_x"] = hx.tolist()
+        # every order on the same workload, a smooth workload, and the scalar
+        # advection throughput case (each: 1 warm-up step, 2 timed steps)
+        def rate(solver, Ustate, steps=2, dt=0.0):
+            solver.step(Ustate, dt, a.cfl)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record()
+            for _ in range(steps):
+                solver.step(Ustate, dt, a.cfl)
+            f1.record()
+            torch.cuda.synchronize()
+            return Ustate[0].numel() * 3 * steps / (f0.elapsed_time(f1) * 1e-3)
+        per_order = {}
+        for Rk in enomr.ORDERS:
+            sk = enomr.Solver(enomr.EULER, (n, n), order=Rk, dx=dx, dy=dy,
+                              bc=enomr.TRANSMISSIVE, device=dev)
+            per_order[str(Rk)] = rate(sk, torch.from_numpy(U0).to(dev))
+            sk.close()
+        extras["per_order_riemann"] = {"unit": UNIT, "values": per_order}
+        Uv, hv, _ = workloads.isentropic_vortex(n)
+        sv = enomr.Solver(enomr.EULER, (n, n), order=R, dx=hv, dy=hv, bc=enomr.PERIODIC,
+                          device=dev)
+        extras["smooth_vortex"] = {"workload": f"isentropic vortex {n}^2 periodic, order {R}",
+                                   "value": rate(sv, torch.from_numpy(Uv).to(dev)), "unit": UNIT}
+        sv.close()
+        adv = {}
+        for Rk in (5, 9, 17):
+            ua, ha = workloads.advection_sine(1 << 24)
+            sa = enomr.Solver(enomr.ADVECTION, 1 << 24, order=Rk, dx=ha, bc=enomr.PERIODIC,
+                              device=dev)
+            ud = torch.from_numpy(ua).to(dev).view(1, -1).squeeze(0)
+            sa.step(ud, 0.5 * ha)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record()
+            for _ in range(4):
+                sa.step(ud, 0.5 * ha)
+            f1.record()
+            torch.cuda.synchronize()
+            adv[str(Rk)] = ua.size * 3 * 4 / (f0.elapsed_time(f1) * 1e-3)
+            sa.close()
+        extras["advection_2p24"] = {"workload": "advection sin(pi x), N=2^24, periodic",
+                                    "unit": UNIT, "values": adv}
+        extras["batched"] = batched_gain(enomr, workloads, dev, a)
         # end to end through the public API with host buffers
         Uh_in = torch.from_numpy(U0).pin_memory()
         Uh_out = torch.empty_like(Uh_in).pin_memory()

@@ -146,6 +146,49 @@ ENOMR_API enomr_status enomr_debug_selection(enomr_ctx *ctx, const double *U, ui
 ENOMR_API enomr_status enomr_get_status(enomr_ctx *ctx);
 
 /*
+ * Batched problems: many independent 1D Euler problems of uneven size
+ * advanced together, one persistent launch per SSP-RK3 stage.
+ *
+ * Packing: problem p's state is a dense [3][n[p]] block (rho, rho u, rho e);
+ * the blocks follow each other in problem order in one device array, so
+ * problem p starts at 3 * (n[0] + ... + n[p-1]) doubles.
+ * Each problem has its own spacing dx[p], split speeds alpha_k (over its own
+ * cells, Eq. LF_Flux_Split) and CFL step; boundaries and order are shared.
+ * The per-interface, per-cell and per-problem arithmetic equals that of
+ * enomr_step() with dt <= 0 on the problem alone, so every problem's result
+ * is bitwise the same as advancing it on its own.
+ */
+typedef struct enomr_batch enomr_batch;
+
+/* enomr_batch_init -- n (host, nprob entries, each >= 1; periodic needs
+ * n >= order+1), dx (host, nprob entries > 0), order, gamma, bc, stream as in
+ * enomr_init().  Builds the tile tables and allocates the scratch (two stage
+ * buffers, per-problem alpha and dt). */
+ENOMR_API enomr_status enomr_batch_init(enomr_batch **out, int64_t nprob, const int64_t *n,
+                                        const double *dx, int order, double gamma, int bc,
+                                        void *stream);
+ENOMR_API void enomr_batch_free(enomr_batch *b);
+ENOMR_API enomr_status enomr_batch_set_stream(enomr_batch *b, void *stream);
+/* enomr_batch_total_cells -- sum of n (or -1 for NULL). */
+ENOMR_API int64_t enomr_batch_total_cells(const enomr_batch *b);
+
+/* enomr_batch_step -- one SSP-RK3 step in place on the packed state U
+ * (device), each problem with its own CFL step cfl*dx[p]/max(|u|+c).
+ * Launches: alpha of U^n, per-problem dt, three persistent stage kernels.
+ * Does not synchronise; no allocation (graph-capturable by the caller). */
+ENOMR_API enomr_status enomr_batch_step(enomr_batch *b, double *U, double cfl);
+
+/* enomr_batch_autotune -- time the stage kernel on state U (read only) for
+ * every tile size (32, 64, 128 interfaces) and persistent grid (2, 4, 8, 16
+ * CTAs per SM), reps launches each, and keep the fastest for later steps.
+ * *tile and *grid (host, may be NULL) receive the choice.  Synchronises. */
+ENOMR_API enomr_status enomr_batch_autotune(enomr_batch *b, const double *U, int reps, int *tile,
+                                            int *grid);
+
+/* enomr_batch_get_status -- as enomr_get_status(). */
+ENOMR_API enomr_status enomr_batch_get_status(enomr_batch *b);
+
+/*
  * Measurement hooks (not part of the method).
  * enomr_profile_begin -- record CUDA events around the next max_launches
  *   launches of one kernel of this context: 1 = the x sweep (1D: the sweep,

@@ -9,6 +9,7 @@
 #include <new>
 
 #include "../../include/enomr.h"
+#include "enomr_common.cuh"
 #include "enomr_internal.h"
 
 using namespace enomr;
@@ -66,14 +67,10 @@ __global__ void __launch_bounds__(256) k_alpha(AlphaArgs A)
         unsigned long long rm[3] = {0, 0, 0};
         if (x < A.nx && y < A.ny) {
             const long long i = y * A.nx + x;
-            const double rho = A.U[i];
-            const double ir = 1.0 / rho;
-            const double u = A.U[ncell + i] * ir;
-            const double v = (C == 4) ? A.U[2 * ncell + i] * ir : 0.0;
-            const double E = A.U[(C - 1) * ncell + i];
-            const double p = A.gm1 * (E - 0.5 * rho * (u * u + v * v));
-            if (!(rho > 0.0) || !(p > 0.0) || !(fabs(E) < 1e300)) atomicOr(A.status, ST_NONPHYS_CELL);
-            const double c = sqrt(A.gamma * p * ir);
+            const CellWaves cw = cell_waves<C>(A.U[i], A.U[ncell + i],
+                                               (C == 4) ? A.U[2 * ncell + i] : 0.0,
+                                               A.U[(C - 1) * ncell + i], A.gm1, A.gamma, A.status);
+            const double u = cw.u, v = cw.v, c = cw.c;
             rm[0] = __double_as_longlong(fabs(u - c));
             rm[1] = __double_as_longlong(fabs(u));
             rm[2] = __double_as_longlong(fabs(u + c));
@@ -231,6 +228,7 @@ static SweepArgs sweep_args(enomr_ctx *c, const double *U, bool ysweep)
     a.inv_gm1 = 1.0 / (c->gamma - 1.0);
     a.inv_h = 1.0 / (ysweep ? c->dy : c->dx);
     a.alpha = ysweep ? c->ay : c->ax;
+    a.alpha_next = nullptr;
     a.sel = nullptr;
     a.status = c->status;
     memset(&a.epi, 0, sizeof(a.epi));
@@ -405,9 +403,9 @@ static const double RK_C0[3] = {0.0, 0.75, 1.0 / 3.0};
 static const double RK_C1[3] = {1.0, 0.25, 2.0 / 3.0};
 
 static enomr_status stage_impl(enomr_ctx *c, int s, const double *Un, const double *Us,
-                               double *Uout)
+                               double *Uout, bool alpha_current = false)
 {
-    enomr_status st = compute_alpha(c, Us, false);
+    enomr_status st = alpha_current ? ENOMR_OK : compute_alpha(c, Us, false);
     if (st) return st;
     Epilogue e;
     memset(&e, 0, sizeof(e));
@@ -449,7 +447,9 @@ ENOMR_API enomr_status enomr_step(enomr_ctx *c, double *U, double dt, double cfl
     if (!c || !U) return ENOMR_EINVAL;
     enomr_status st = set_step_dt(c, U, dt, cfl);
     if (st) return st;
-    if ((st = stage_impl(c, 1, U, U, c->U1))) return st;
+    // with a CFL step the alpha of U^n was just computed with the wave-speed max
+    const bool alpha_done = !(dt > 0.0) && c->eq != ENOMR_ADVECTION;
+    if ((st = stage_impl(c, 1, U, U, c->U1, alpha_done))) return st;
     if ((st = stage_impl(c, 2, U, c->U1, c->U2))) return st;
     if ((st = stage_impl(c, 3, U, c->U2, U))) return st;
     if (dt_used) {

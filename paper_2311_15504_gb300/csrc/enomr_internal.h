@@ -33,6 +33,7 @@ struct SweepArgs {
     double gm1, inv_gm1, gamma;
     double inv_h;
     const double *alpha;   // [lines][3]: max|un-c|, max|un|, max|un+c|
+    double *alpha_next;    // 1D only: accumulate the output state's alpha here, or nullptr
     uint8_t *sel;          // optional selection dump for this sweep
     int *status;
     Epilogue epi;
@@ -56,6 +57,46 @@ struct AlphaArgs {
     double *smax;          // CFL wave-speed max (may be nullptr)
     int *status;
 };
+
+// Batched 1D Euler (problem-major packing: problem p's [3][n_p] block starts
+// at base[p]).
+struct BatchTile {
+    int prob;  // problem index
+    int x0;    // first interface of the tile
+};
+
+struct BatchArgs {
+    const double *Us, *Un;
+    double *out;
+    const long long *base, *n;
+    const double *inv_dx;
+    const double *alpha;   // [nprob][3] of Us
+    double *alpha_next;    // [nprob][3] of out, or nullptr
+    const double *dt;      // [nprob]
+    const BatchTile *tiles;
+    long long ntiles;
+    int bc;
+    double gm1, inv_gm1, gamma, c0, c1;
+    int *status;
+};
+
+struct BatchAlphaArgs {
+    const double *U;
+    const long long *base, *n;
+    const double *inv_dx;
+    const BatchTile *tiles;  // tiles of TP - 1 cells
+    long long ntiles;
+    int cells_per_tile;
+    double gm1, gamma, cfl;
+    double *alpha;           // [nprob][3], zeroed before the launch
+    int *status;
+};
+
+template <int R> cudaError_t launch_batch_stage(const BatchArgs &a, int tp, int grid,
+                                                cudaStream_t s);
+cudaError_t launch_batch_alpha(const BatchAlphaArgs &a, cudaStream_t s);
+cudaError_t launch_batch_dt(const double *alpha, const double *inv_dx, double cfl, long long nprob,
+                            double *dt, cudaStream_t s);
 
 template <int R> cudaError_t launch_advection(const AdvArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler1d(const SweepArgs &a, cudaStream_t s);

@@ -32,6 +32,7 @@
 #include <stdint.h>
 
 #include "enomr_coeffs.h"
+#include "enomr_common.cuh"
 #include "enomr_internal.h"
 
 namespace enomr {
@@ -139,15 +140,18 @@ __device__ __forceinline__ void load_a_table(double *sA, int tid, int nthreads)
 // ---------------------------------------------------------------------------
 // Epilogue: D -> output
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void epilogue(const Epilogue &e, long long idx, double D, double Us)
+__device__ __forceinline__ double epilogue(const Epilogue &e, long long idx, double D, double Us)
 {
     if (e.Dprev) D = e.Dprev[idx] + D;
+    double o;
     if (e.mode == EPI_STORE) {
-        e.out[idx] = D;
+        o = D;
     } else {
         const double dt = *e.dt_dev;
-        e.out[idx] = e.c0 * e.Un[idx] + e.c1 * fma(dt, D, Us);
+        o = e.c0 * e.Un[idx] + e.c1 * fma(dt, D, Us);
     }
+    e.out[idx] = o;
+    return o;
 }
 
 // ---------------------------------------------------------------------------
@@ -198,26 +202,35 @@ __global__ void __launch_bounds__(TP) k_advection(AdvArgs A)
 // Euler line sweep.  DIR 0: lines are rows (x contiguous); DIR 1: lines are
 // columns.  C = 3 (1D) or 4 (2D, components rho, m_x, m_y, E).
 // ---------------------------------------------------------------------------
+template <int R, int C, int TP, int NL>
+struct SweepSmem {
+    static constexpr int g = (R + 1) / 2, S = TP + 2 * g - 1;
+    double sU[C][NL][S];
+    double sF[C][NL][S];
+    double sP[4][NL][S];  // sqrt(rho), u_n, u_t, H
+    double sFh[C][NL][TP];
+    unsigned long long red[TP * NL / 32][3];
+};
+
+// One tile: NL lines x TP interfaces starting at interface x0 of line l0.
+// All threads of the CTA must call it; it ends after its epilogue.
 template <int R, int C, int DIR, int TP, int NL>
-__global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
+__device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, long long l0,
+                                           const double *sA, SweepSmem<R, C, TP, NL> &sm)
 {
     constexpr int g = (R + 1) / 2, W = 2 * g - 1, S = TP + 2 * g - 1, T = Tab<R>::T;
     constexpr int NT = TP * NL;
     constexpr int QN = (DIR == 0) ? 1 : 2;  // normal momentum component
     constexpr int QT = (DIR == 0) ? 2 : 1;  // tangential momentum component (C = 4)
-    __shared__ double sU[C][NL][S];
-    __shared__ double sF[C][NL][S];
-    __shared__ double sP[4][NL][S];  // sqrt(rho), u_n, u_t, H
-    __shared__ double sFh[C][NL][TP];
-    __shared__ double sA[T * W];
+    auto &sU = sm.sU;
+    auto &sF = sm.sF;
+    auto &sP = sm.sP;
+    auto &sFh = sm.sFh;
 
     const long long nx = A.nx, ny = A.ny, ncell = nx * ny;
     const long long nlen = (DIR == 0) ? nx : ny;
     const long long nlines = (DIR == 0) ? ny : nx;
-    const long long x0 = (long long)((DIR == 0) ? blockIdx.x : blockIdx.y) * (TP - 1);
-    const long long l0 = (long long)((DIR == 0) ? blockIdx.y : blockIdx.x) * NL;
     const int tid = threadIdx.x;
-    load_a_table<R>(sA, tid, NT);
 
     // ---- stage cells, primitives and physical fluxes (normal direction)
     for (int idx = tid; idx < NL * S; idx += NT) {
@@ -237,7 +250,8 @@ __global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
 #pragma unroll
         for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
         const double rho = u[0];
-        const double ir = 1.0 / rho;
+        const double rr = rsqrt(rho);  // 1/sqrt(rho): gives sqrt(rho) and 1/rho
+        const double ir = rr * rr;
         const double un = u[QN] * ir;
         const double ut = (C == 4) ? u[QT] * ir : 0.0;
         const double E = u[C - 1];
@@ -251,7 +265,7 @@ __global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
         sF[1][line][s] = fma(u[QN], un, p);
         if (C == 4) sF[2][line][s] = u[QT] * un;
         sF[C - 1][line][s] = (E + p) * un;
-        sP[0][line][s] = sqrt(rho);
+        sP[0][line][s] = rho * rr;
         sP[1][line][s] = un;
         sP[2][line][s] = ut;
         sP[3][line][s] = (E + p) * ir;
@@ -272,19 +286,31 @@ __global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
     const bool valid = (Lg < nlines) && (k <= nlen);
     const int sl = p + g - 1, sr = p + g;
 
-    // Roe average (Sec. 4)
-    const double qL = sP[0][line][sl], qR = sP[0][line][sr];
-    const double rs = 1.0 / (qL + qR);
-    const double uh = (qL * sP[1][line][sl] + qR * sP[1][line][sr]) * rs;
-    const double vh = (C == 4) ? (qL * sP[2][line][sl] + qR * sP[2][line][sr]) * rs : 0.0;
-    const double Hh = (qL * sP[3][line][sl] + qR * sP[3][line][sr]) * rs;
+    // Roe average (Sec. 4); for two bitwise-equal states it is that state.
+    bool eqLR = true;
+#pragma unroll
+    for (int q = 0; q < C; ++q)
+        eqLR = eqLR && (__double_as_longlong(sU[q][line][sl]) == __double_as_longlong(sU[q][line][sr]));
+    double uh, vh, Hh;
+    if (eqLR) {
+        uh = sP[1][line][sl];
+        vh = (C == 4) ? sP[2][line][sl] : 0.0;
+        Hh = sP[3][line][sl];
+    } else {
+        const double qL = sP[0][line][sl], qR = sP[0][line][sr];
+        const double rs = 1.0 / (qL + qR);
+        uh = (qL * sP[1][line][sl] + qR * sP[1][line][sr]) * rs;
+        vh = (C == 4) ? (qL * sP[2][line][sl] + qR * sP[2][line][sr]) * rs : 0.0;
+        Hh = (qL * sP[3][line][sl] + qR * sP[3][line][sr]) * rs;
+    }
     const double hq = 0.5 * (uh * uh + vh * vh);
     const double c2 = A.gm1 * (Hh - hq);
     if (valid && !(c2 > 0.0)) atomicOr(A.status, ST_NONPHYS_ROE);
-    const double cs = sqrt(c2);
+    const double ic = rsqrt(c2);         // 1/c: one reciprocal square root
+    const double cs = c2 * ic;           // c
     const double kap = cs * A.inv_gm1;   // c / (gamma-1)
     const double c2g = c2 * A.inv_gm1;   // c^2 / (gamma-1)
-    const double b1 = A.gm1 / c2;        // (gamma-1) / c^2
+    const double b1 = A.gm1 * (ic * ic);  // (gamma-1) / c^2
 
     const double *al = A.alpha + 3 * (Lg < nlines ? Lg : nlines - 1);
     const double a_m = al[0], a_0 = al[1], a_p = al[2];
@@ -297,12 +323,11 @@ __global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
     //                                        + hq phi_1 + v phi_2,
     // phi_a being the u+c field.
     double acc_s = 0.0, acc_d = 0.0, ph1 = 0.0, ph2 = 0.0;
-#pragma unroll 1
-    for (int f = 0; f < C; ++f) {
-        // scaled left-eigenvector row with a unit entry
-        const bool shear = (C == 4 && f == 2);
-        double l0c, l1c, alpha;
-        if (shear) {
+
+    // Scaled left-eigenvector row of field f (a unit entry on E, or on the
+    // tangential momentum for the shear field) and the split speed alpha_f.
+    auto row = [&](int f, double &l0c, double &l1c, double &alpha) {
+        if (C == 4 && f == 2) {
             l0c = -vh;
             l1c = 0.0;
             alpha = a_0;
@@ -319,33 +344,26 @@ __global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
             l1c = -uh;
             alpha = a_0;
         }
-        double vp[W], vm[W];
-#pragma unroll
-        for (int j = 0; j < 2 * g; ++j) {
-            const int s = p + j;
-            double w, q;
-            if (shear) {
-                w = fma(l0c, sU[0][line][s], sU[2][line][s]);
-                q = fma(l0c, sF[0][line][s], sF[2][line][s]);
-            } else {
-                w = sU[C - 1][line][s];
-                q = sF[C - 1][line][s];
-                if (C == 4) {
-                    w = fma(-vh, sU[2][line][s], w);
-                    q = fma(-vh, sF[2][line][s], q);
-                }
-                w = fma(l1c, sU[1][line][s], w);
-                q = fma(l1c, sF[1][line][s], q);
-                w = fma(l0c, sU[0][line][s], w);
-                q = fma(l0c, sF[0][line][s], q);
+    };
+    // w = l U and q = l F of staged cell s (the same operations on every path).
+    auto project = [&](int f, int s, double l0c, double l1c, double &w, double &q) {
+        if (C == 4 && f == 2) {
+            w = fma(l0c, sU[0][line][s], sU[2][line][s]);
+            q = fma(l0c, sF[0][line][s], sF[2][line][s]);
+        } else {
+            w = sU[C - 1][line][s];
+            q = sF[C - 1][line][s];
+            if (C == 4) {
+                w = fma(-vh, sU[2][line][s], w);
+                q = fma(-vh, sF[2][line][s], q);
             }
-            if (j <= 2 * g - 2) vp[j] = fma(alpha, w, q);           // cell k-1+l, l = j-(g-1)
-            if (j >= 1) vm[2 * g - 1 - j] = fma(-alpha, w, q);      // cell k-l,   l = g-j
+            w = fma(l1c, sU[1][line][s], w);
+            q = fma(l1c, sF[1][line][s], q);
+            w = fma(l0c, sU[0][line][s], w);
+            q = fma(l0c, sF[0][line][s], q);
         }
-        int selp, selm;
-        const double fp = mr_value<R>(vp, sA, valid, selp);
-        const double fm = mr_value<R>(vm, sA, valid, selm);
-        const double ft = fp + fm;
+    };
+    auto accumulate = [&](int f, double ft) {
         if (f == 0) {
             const double ph = 0.25 * b1 * ft;
             acc_s += ph;
@@ -354,15 +372,69 @@ __global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
             const double ph = 0.25 * b1 * ft;
             acc_s += ph;
             acc_d += ph;
-        } else if (shear) {
+        } else if (C == 4 && f == 2) {
             ph2 = 0.5 * ft;
         } else {
             ph1 = -0.5 * b1 * ft;
         }
-        if (A.sel && valid) {
-            const long long NI = nlen + 1;
-            A.sel[((0 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selp;
-            A.sel[((1 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selm;
+    };
+
+    // Flat windows.  If the states of three consecutive cells ending or
+    // starting at a side's centre are bitwise equal, every field's projected
+    // values there are bitwise equal too, so that side's IS_0 is exactly 0,
+    // no candidate is tested and minmod returns v(0): only the centre cell
+    // needs projecting.  The result is the same as on the full path.
+    auto same = [&](int a, int b) {
+        bool e = true;
+#pragma unroll
+        for (int q = 0; q < C; ++q)
+            e = e && (__double_as_longlong(sU[q][line][a]) == __double_as_longlong(sU[q][line][b]));
+        return e;
+    };
+    const bool e0 = same(sl - 2, sl - 1), e1 = same(sl - 1, sl), e2 = same(sl, sr),
+               e3 = same(sr, sr + 1), e4 = same(sr + 1, sr + 2);
+    const bool plus_flat = (e0 && e1) || (e2 && e3);   // centre cell k-1
+    const bool minus_flat = (e3 && e4) || (e1 && e2);  // centre cell k (mirrored)
+    const bool flat = plus_flat && minus_flat;
+
+    if (__all_sync(FULL, flat || !valid)) {
+#pragma unroll 1
+        for (int f = 0; f < C; ++f) {
+            double l0c, l1c, alpha, w, q;
+            row(f, l0c, l1c, alpha);
+            project(f, sl, l0c, l1c, w, q);
+            const double fp = fma(alpha, w, q);
+            project(f, sr, l0c, l1c, w, q);
+            const double fm = fma(-alpha, w, q);
+            accumulate(f, fp + fm);
+            if (A.sel && valid) {
+                const long long NI = nlen + 1;
+                A.sel[((0 * C + f) * nlines + Lg) * NI + k] = (uint8_t)(T + 2);
+                A.sel[((1 * C + f) * nlines + Lg) * NI + k] = (uint8_t)(T + 2);
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int f = 0; f < C; ++f) {
+            double l0c, l1c, alpha;
+            row(f, l0c, l1c, alpha);
+            double vp[W], vm[W];
+#pragma unroll
+            for (int j = 0; j < 2 * g; ++j) {
+                double w, q;
+                project(f, p + j, l0c, l1c, w, q);
+                if (j <= 2 * g - 2) vp[j] = fma(alpha, w, q);       // cell k-1+l, l = j-(g-1)
+                if (j >= 1) vm[2 * g - 1 - j] = fma(-alpha, w, q);  // cell k-l,   l = g-j
+            }
+            int selp, selm;
+            const double fp = mr_value<R>(vp, sA, valid, selp);
+            const double fm = mr_value<R>(vm, sA, valid, selm);
+            accumulate(f, fp + fm);
+            if (A.sel && valid) {
+                const long long NI = nlen + 1;
+                A.sel[((0 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selp;
+                A.sel[((1 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selm;
+            }
         }
     }
     double Fh[C];
@@ -375,19 +447,100 @@ __global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
     __syncthreads();
 
     // ---- flux difference and epilogue for the TP-1 cells of the tile
+    unsigned long long ws[3] = {0, 0, 0};
     if (p < TP - 1 && Lg < nlines) {
         const long long i = x0 + p;
         if (i < nlen) {
             const long long gi = (DIR == 0) ? Lg * nx + i : i * nx + Lg;
             const int sc = p + g;  // staged index of cell i
+            double o[C];
 #pragma unroll
             for (int q = 0; q < C; ++q) {
                 // map line component back to the state component
                 const int qs = (q == 1) ? QN : ((C == 4 && q == 2) ? QT : q);
                 const double D = -(sFh[q][line][p + 1] - sFh[q][line][p]) * A.inv_h;
-                epilogue(A.epi, qs * ncell + gi, D, sU[q][line][sc]);
+                o[q] = epilogue(A.epi, qs * ncell + gi, D, sU[q][line][sc]);
+            }
+            if (C == 3 && A.alpha_next) {
+                double w3[3];
+                wave_speeds3(o[0], o[1], o[2], A.gm1, A.gamma, w3, A.status);
+#pragma unroll
+                for (int k3 = 0; k3 < 3; ++k3) ws[k3] = __double_as_longlong(w3[k3]);
             }
         }
+    }
+    if (C == 3 && A.alpha_next) {
+        // CTA maximum of the new state's wave speeds -> the next stage's alpha
+#pragma unroll
+        for (int k3 = 0; k3 < 3; ++k3) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long w = __shfl_xor_sync(FULL, ws[k3], o);
+                ws[k3] = ws[k3] > w ? ws[k3] : w;
+            }
+        }
+        if ((tid & 31) == 0)
+            for (int k3 = 0; k3 < 3; ++k3) sm.red[tid >> 5][k3] = ws[k3];
+        __syncthreads();
+        if (tid < 3) {
+            unsigned long long m = 0;
+            for (int wi = 0; wi < NT / 32; ++wi) m = m > sm.red[wi][tid] ? m : sm.red[wi][tid];
+            atomicMax((unsigned long long *)(A.alpha_next + tid), m);
+        }
+    }
+}
+
+template <int R, int C, int DIR, int TP, int NL>
+__global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
+{
+    constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
+    __shared__ SweepSmem<R, C, TP, NL> sm;
+    __shared__ double sA[T * W];
+    load_a_table<R>(sA, threadIdx.x, TP * NL);
+    const long long x0 = (long long)((DIR == 0) ? blockIdx.x : blockIdx.y) * (TP - 1);
+    const long long l0 = (long long)((DIR == 0) ? blockIdx.y : blockIdx.x) * NL;
+    sweep_tile<R, C, DIR, TP, NL>(A, x0, l0, sA, sm);
+}
+
+// ---------------------------------------------------------------------------
+// Batched 1D Euler: one persistent launch per RK stage over a table of
+// (problem, first interface) tiles of many independent problems of uneven
+// size.  Each tile runs the same interface arithmetic as the single-problem
+// sweep, so results are bitwise those of one problem at a time.
+// ---------------------------------------------------------------------------
+template <int R, int TP>
+__global__ void __launch_bounds__(TP) k_batch_stage(BatchArgs B)
+{
+    constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
+    __shared__ SweepSmem<R, 3, TP, 1> sm;
+    __shared__ double sA[T * W];
+    load_a_table<R>(sA, threadIdx.x, TP);
+    for (long long t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
+        __syncthreads();  // the previous tile is done with shared memory
+        const BatchTile tl = B.tiles[t];
+        const int pr = tl.prob;
+        const long long base = B.base[pr];
+        SweepArgs A;
+        A.U = B.Us + base;
+        A.nx = B.n[pr];
+        A.ny = 1;
+        A.bc = B.bc;
+        A.gm1 = B.gm1;
+        A.inv_gm1 = B.inv_gm1;
+        A.gamma = B.gamma;
+        A.inv_h = B.inv_dx[pr];
+        A.alpha = B.alpha + 3 * pr;
+        A.alpha_next = B.alpha_next ? B.alpha_next + 3 * pr : nullptr;
+        A.sel = nullptr;
+        A.status = B.status;
+        A.epi.mode = EPI_STAGE;
+        A.epi.c0 = B.c0;
+        A.epi.c1 = B.c1;
+        A.epi.dt_dev = B.dt + pr;
+        A.epi.Un = B.Un + base;
+        A.epi.Dprev = nullptr;
+        A.epi.out = B.out + base;
+        sweep_tile<R, 3, 0, TP, 1>(A, tl.x0, 0, sA, sm);
     }
 }
 

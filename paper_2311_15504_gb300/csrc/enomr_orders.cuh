@@ -49,3 +49,21 @@ template cudaError_t launch_euler2d_x<ENOMR_R>(const SweepArgs &, cudaStream_t);
 template cudaError_t launch_euler2d_y<ENOMR_R>(const SweepArgs &, cudaStream_t);
 
 }  // namespace enomr
+
+namespace enomr {
+
+template <int R> cudaError_t launch_batch_stage(const BatchArgs &a, int tp, int grid,
+                                                cudaStream_t s)
+{
+    switch (tp) {
+    case 32: k_batch_stage<R, 32><<<grid, 32, 0, s>>>(a); break;
+    case 64: k_batch_stage<R, 64><<<grid, 64, 0, s>>>(a); break;
+    case 128: k_batch_stage<R, 128><<<grid, 128, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_batch_stage<ENOMR_R>(const BatchArgs &, int, int, cudaStream_t);
+
+}  // namespace enomr

@@ -44,6 +44,13 @@ _SIGS = {
     "enomr_probe_fp64_fma": (_I, [_P, ctypes.c_int64, _P, ctypes.POINTER(_D),
                                  ctypes.POINTER(_D)]),
     "enomr_rhs_euler2d_noalloc": (_I, [_P, _P, _L, _L, _D, _D, _I, _D, _I, _P]),
+    "enomr_batch_init": (_I, [ctypes.POINTER(_P), _L, _P, _P, _I, _D, _I, _P]),
+    "enomr_batch_free": (None, [_P]),
+    "enomr_batch_set_stream": (_I, [_P, _P]),
+    "enomr_batch_total_cells": (_L, [_P]),
+    "enomr_batch_step": (_I, [_P, _P, _D]),
+    "enomr_batch_autotune": (_I, [_P, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "enomr_batch_get_status": (_I, [_P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -188,6 +195,69 @@ class Solver:
     def close(self):
         if getattr(self, "_ctx", None):
             _lib.enomr_free(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent 1D Euler problems advanced together (one persistent
+    launch per RK stage).  State: one float64 CUDA tensor of 3 * sum(n)
+    values, problem p's [3, n[p]] block after problem p-1's."""
+
+    def __init__(self, sizes, dx, order=9, bc=TRANSMISSIVE, gamma=1.4, device=None):
+        import numpy as np
+        self.sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+        self.dx = np.ascontiguousarray(dx, dtype=np.float64)
+        if self.sizes.shape != self.dx.shape or self.sizes.ndim != 1:
+            raise ValueError("sizes and dx must be 1D arrays of the same length")
+        self.device = torch.device(device if device is not None else "cuda")
+        self.offsets = np.concatenate([[0], np.cumsum(3 * self.sizes)])
+        ctx = _P()
+        with torch.cuda.device(self.device):
+            s = torch.cuda.current_stream(self.device).cuda_stream
+            _check(_lib.enomr_batch_init(ctypes.byref(ctx), len(self.sizes),
+                                         self.sizes.ctypes.data_as(_P),
+                                         self.dx.ctypes.data_as(_P), order, gamma, bc, _P(s)),
+                   "enomr_batch_init")
+        self._ctx = ctx
+        self.total = int(_lib.enomr_batch_total_cells(ctx))
+
+    def _state(self, U):
+        if (not isinstance(U, torch.Tensor) or U.dtype != torch.float64 or U.device.type != "cuda"
+                or U.numel() != 3 * self.total or not U.is_contiguous()):
+            raise ValueError(f"packed state must be a contiguous float64 CUDA tensor of {3 * self.total}")
+        _check(_lib.enomr_batch_set_stream(self._ctx,
+                                           _P(torch.cuda.current_stream(self.device).cuda_stream)),
+               "enomr_batch_set_stream")
+        return _P(U.data_ptr())
+
+    def pack(self, states):
+        return torch.cat([torch.as_tensor(u, dtype=torch.float64).reshape(-1) for u in states]).to(
+            self.device)
+
+    def view(self, U, p):
+        return U[int(self.offsets[p]):int(self.offsets[p + 1])].view(3, int(self.sizes[p]))
+
+    def step(self, U, cfl=0.5):
+        _check(_lib.enomr_batch_step(self._ctx, self._state(U), float(cfl)), "enomr_batch_step")
+
+    def autotune(self, U, reps=3):
+        t, g = _I(), _I()
+        _check(_lib.enomr_batch_autotune(self._ctx, self._state(U), int(reps), ctypes.byref(t),
+                                         ctypes.byref(g)), "enomr_batch_autotune")
+        return t.value, g.value
+
+    def check_status(self):
+        _check(_lib.enomr_batch_get_status(self._ctx), "enomr_batch_get_status")
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            _lib.enomr_batch_free(self._ctx)
             self._ctx = None
 
     def __del__(self):

@@ -96,3 +96,23 @@ def test_generated_coefficients_are_fresh_and_exact():
                 for s, x in enumerate(w):
                     want[s - m + g - 1] = float(Fraction(x))
                 assert row == want, (R, t, name)
+
+
+def test_batch_host_side_argument_checks(lib):
+    import numpy as np
+    L = lib._lib
+    ctx = ctypes.c_void_p()
+    P = ctypes.c_void_p
+    n = np.array([100, 0, 50], dtype=np.int64)
+    dx = np.array([0.1, 0.1, 0.1])
+    assert L.enomr_batch_init(ctypes.byref(ctx), 3, n.ctypes.data_as(P), dx.ctypes.data_as(P),
+                              9, 1.4, 1, P(0)) == 1
+    n[1] = 5
+    assert L.enomr_batch_init(ctypes.byref(ctx), 3, n.ctypes.data_as(P), dx.ctypes.data_as(P),
+                              9, 1.4, 0, P(0)) == 1  # periodic needs n >= 2g
+    dx[2] = 0.0
+    assert L.enomr_batch_init(ctypes.byref(ctx), 3, n.ctypes.data_as(P), dx.ctypes.data_as(P),
+                              9, 1.4, 1, P(0)) == 1
+    assert L.enomr_batch_step(None, None, 0.5) == 1
+    assert L.enomr_batch_total_cells(None) == -1
+    L.enomr_batch_free(None)

@@ -238,3 +238,31 @@ def test_constant_state_and_scale_properties(E):
     r2 = a.rhs(dev(u * 2.0 ** 40))
     assert torch.equal(r2, r1 * 2.0 ** 40)
     assert torch.equal(a.selection(dev(u)), a.selection(dev(u * 2.0 ** 40)))
+
+
+@pytest.mark.parametrize("R", [5, 9, 17])
+def test_euler2d_rhs_evolved_state(E, R):
+    """Parity on a Riemann state advanced 25 CFL steps on the GPU: smeared
+    fronts next to exactly flat regions, so warps mix the flat-window path
+    and the full path."""
+    nx, ny = 300, 140
+    U, dx, dy = wl.riemann2d(nx, ny, seed=20 + R)
+    s = E.Solver(E.EULER, (ny, nx), order=R, dx=dx, dy=dy, bc=1)
+    Ud = dev(U)
+    for _ in range(25):
+        s.step(Ud, 0.0, 0.5)
+    U = Ud.cpu().numpy()
+    sel = s.selection(Ud).cpu().numpy()
+    ref = oracle.rhs_euler2d(U, dx, dy, R, bc=1, want_sel=True, want_win=True)
+    nsx = 8 * ny * (nx + 1)
+    fx = euler_scale_fn(lambda y: U[:, y, :].T.copy(), ny, nx, R, 1, lambda y: ref["alpha_x"][y])
+    fy = euler_scale_fn(lambda x: U[[0, 2, 1, 3], :, x].T.copy(), nx, ny, R, 1,
+                        lambda x: ref["alpha_y"][x])
+    assert_selection(R, sel[:nsx], ref["sel_x"], ref["win_x"], f"evolved-x R={R}", fx)
+    assert_selection(R, sel[nsx:], ref["sel_y"], ref["win_y"], f"evolved-y R={R}", fy)
+    T = oracle.num_tested(R)
+    assert (sel < T + 2).sum() > 100  # non-trivial selections present
+    forced = oracle.rhs_euler2d(U, dx, dy, R, bc=1, forced=sel)
+    got = s.rhs(Ud).cpu().numpy()
+    assert_values(got, forced["rhs"], euler_flux_scale(U) / min(dx, dy), f"evolved R={R}")
+    s.check_status()
