@@ -222,6 +222,42 @@ def batched_gain(enomr, workloads, dev, a, nprob=4096, order=9, reps=5):
             "gain": ms_p / ms_b, "bitwise_identical_after_2_steps": identical}
 
 
+def adjoint_ratio(enomr, workloads, dev, n=1024, order=9, steps=10):
+    """Isentropic vortex (periodic, order 9): time of one SSP-RK3 step
+    against one step of the adjoint (stage recomputation from the step's
+    checkpoint, three RHS transposes, the RK transpose)."""
+    import torch
+    U0, h, _ = workloads.isentropic_vortex(n)
+    s = enomr.Solver(enomr.EULER, (n, n), order=order, dx=h, dy=h, bc=enomr.PERIODIC,
+                     device=dev)
+    U = torch.from_numpy(U0).to(dev)
+    dt = s.cfl_dt(U, 0.5)
+    ck = [U.clone() for _ in range(steps)]
+    g = torch.randn_like(U)
+    out = torch.empty_like(U)
+    s.step(U, dt=dt)
+    s.step_vjp(ck[0], dt, g, out=out)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    for i in range(steps):
+        ck[i].copy_(U)
+        s.step(U, dt=dt)
+    e[1].record()
+    e[2].record()
+    for i in reversed(range(steps)):
+        s.step_vjp(ck[i], dt, g, out=out)
+        g, out = out, g
+    e[3].record()
+    torch.cuda.synchronize()
+    fwd = e[0].elapsed_time(e[1]) / steps
+    bwd = e[2].elapsed_time(e[3]) / steps
+    s.close()
+    return {"workload": f"isentropic vortex {n}^2 periodic, order {order}, fixed dt",
+            "forward_ms_per_step": fwd, "adjoint_ms_per_step": bwd, "ratio": bwd / fwd,
+            "forward_includes_checkpoint_copy": True}
+
+
 def main_ours(a):
     import torch
     import torch.distributed as dist
@@ -361,6 +397,7 @@ def main_ours(a):
         extras["advection_2p24"] = {"workload": "advection sin(pi x), N=2^24, periodic",
                                     "unit": UNIT, "values": adv}
         extras["batched"] = batched_gain(enomr, workloads, dev, a)
+        extras["adjoint"] = adjoint_ratio(enomr, workloads, dev)
         # end to end through the public API with host buffers
         Uh_in = torch.from_numpy(U0).pin_memory()
         Uh_out = torch.empty_like(Uh_in).pin_memory()

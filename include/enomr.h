@@ -146,6 +146,41 @@ ENOMR_API enomr_status enomr_debug_selection(enomr_ctx *ctx, const double *U, ui
 ENOMR_API enomr_status enomr_get_status(enomr_ctx *ctx);
 
 /*
+ * Adjoint.  With the discrete choices of the forward pass frozen -- the
+ * stencil (or minmod branch) chosen at every interface, field and side, and
+ * the cell attaining each per-line alpha -- L is a smooth function of U.
+ * The paper has no adjoint; these are its exact transposes.
+ *
+ * enomr_rhs_vjp -- Ubar = scale * J(U)^T Lbar (accumulate = 0) or
+ *   Ubar += scale * J(U)^T Lbar (accumulate != 0), J = dL/dU at U with the
+ *   choices L(U) makes.  U, Lbar, Ubar: device, state layout; Ubar must not
+ *   alias U or Lbar.  Contributions of cells shared by neighbouring tiles
+ *   are added with atomics, so the last bits may vary from run to run.
+ */
+ENOMR_API enomr_status enomr_rhs_vjp(enomr_ctx *ctx, const double *U, const double *Lbar,
+                                     double *Ubar, double scale, int accumulate);
+
+/* enomr_debug_alpha -- copy (device to device, on the context's stream) the
+ * per-line split speeds alpha [lines][3] (max|u-c|, max|u|, max|u+c|) of the
+ * last enomr_rhs/enomr_stage/enomr_rhs_vjp call, and the alpha cotangents
+ * and the frozen maximising cells (index along the line) of the last
+ * enomr_rhs_vjp call; x-sweep rows [ny][3] and, in 2D, y-sweep columns
+ * [nx][3].  Any pointer may be NULL.  A diagnostic of the adjoint. */
+ENOMR_API enomr_status enomr_debug_alpha(enomr_ctx *ctx, double *alpha_x, double *alpha_y,
+                                         double *alpha_bar_x, double *alpha_bar_y,
+                                         uint64_t *argmax_x, uint64_t *argmax_y);
+
+/*
+ * enomr_step_vjp -- transpose of one SSP-RK3 step (Eq. TVD3rdRK) taken from
+ *   U_n with step dt (> 0, held fixed): U_n_bar = (dU_{n+1}/dU_n)^T U_np1_bar.
+ *   The stage states are recomputed from U_n (a per-step checkpoint) in the
+ *   context's stage buffers; three enomr_rhs_vjp evaluations follow.
+ *   U_n_bar is overwritten and must not alias U_n or U_np1_bar.
+ */
+ENOMR_API enomr_status enomr_step_vjp(enomr_ctx *ctx, const double *U_n, double dt,
+                                      const double *U_np1_bar, double *U_n_bar);
+
+/*
  * Batched problems: many independent 1D Euler problems of uneven size
  * advanced together, one persistent launch per SSP-RK3 stage.
  *

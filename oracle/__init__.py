@@ -73,6 +73,9 @@ def _load():
                 "orc_rhs_euler1d": (I, [L, P, D, I, I, D, P, P, P, P, P, P]),
                 "orc_rhs_euler2d": (I, [L, L, P, D, D, I, I, D, P, P, P, P, P, P, P]),
                 "orc_euler_eigen": (I, [I, D, P, P, P, P, P]),
+                "orc_rhs_euler1d_frozen": (I, [L, P, D, I, I, D, P, P, P, P]),
+                "orc_rhs_euler2d_frozen": (I, [L, L, P, D, D, I, I, D, P, P, P, P, P, P]),
+                "orc_rhs_euler2d_alpha": (I, [L, L, P, D, D, I, I, D, P, P, P, P]),
                 "orc_rhs": (I, [I, L, L, D, D, I, I, D, D, P, P]),
                 "orc_cfl_dt": (I, [I, L, L, D, D, D, D, P, D, P]),
                 "orc_step_ssprk3": (I, [I, L, L, D, D, I, I, D, D, P, D]),
@@ -241,6 +244,51 @@ def rhs_euler2d(U, dx, dy, R, bc=BC_TRANSMISSIVE, gamma=1.4, forced=None, want_s
     if want_count:
         out["ntested"] = cnt.value
     return out
+
+
+def rhs_euler1d_frozen(U, h, R, forced, amax=None, bc=BC_TRANSMISSIVE, gamma=1.4):
+    """1D Euler RHS with the stencils forced and the alpha maximisers given
+    (amax, 3 ints); with amax None returns (rhs, the plain scheme's amax)."""
+    U = _f64(U)
+    N = U.shape[1]
+    rhs = np.zeros_like(U)
+    fz = np.ascontiguousarray(forced, dtype=np.uint8)
+    ain = None if amax is None else np.ascontiguousarray(amax, dtype=np.int32)
+    aout = np.zeros(3, dtype=np.int32)
+    _check(_load().orc_rhs_euler1d_frozen(N, _p(U), h, R, bc, gamma, _p(fz), _p(ain), _p(aout),
+                                          _p(rhs)))
+    return rhs if amax is not None else (rhs, aout)
+
+
+def rhs_euler2d_frozen(U, dx, dy, R, forced, amax=None, bc=BC_TRANSMISSIVE, gamma=1.4):
+    """2D Euler RHS with the stencils forced and the per-line alpha
+    maximisers given (amax = (amx [ny,4], amy [nx,4]))."""
+    U = _f64(U)
+    ny, nx = U.shape[1], U.shape[2]
+    rhs = np.zeros_like(U)
+    fz = np.ascontiguousarray(forced, dtype=np.uint8)
+    if amax is None:
+        ax, ay = np.zeros((ny, 4), dtype=np.int32), np.zeros((nx, 4), dtype=np.int32)
+        _check(_load().orc_rhs_euler2d_frozen(nx, ny, _p(U), dx, dy, R, bc, gamma, _p(fz), None,
+                                              None, _p(ax), _p(ay), _p(rhs)))
+        return rhs, (ax, ay)
+    ax = np.ascontiguousarray(amax[0], dtype=np.int32)
+    ay = np.ascontiguousarray(amax[1], dtype=np.int32)
+    _check(_load().orc_rhs_euler2d_frozen(nx, ny, _p(U), dx, dy, R, bc, gamma, _p(fz), _p(ax),
+                                          _p(ay), None, None, _p(rhs)))
+    return rhs
+
+
+def rhs_euler2d_alpha(U, dx, dy, R, forced, alpha_x, alpha_y, bc=BC_TRANSMISSIVE, gamma=1.4):
+    """2D Euler RHS with forced stencils and given split speeds
+    (alpha_x [ny,4], alpha_y [nx,4])."""
+    U = _f64(U)
+    ny, nx = U.shape[1], U.shape[2]
+    rhs = np.zeros_like(U)
+    fz = np.ascontiguousarray(forced, dtype=np.uint8)
+    _check(_load().orc_rhs_euler2d_alpha(nx, ny, _p(U), dx, dy, R, bc, gamma, _p(fz),
+                                         _p(_f64(alpha_x)), _p(_f64(alpha_y)), _p(rhs)))
+    return rhs
 
 
 def euler_eigen(UL, UR, gamma=1.4):

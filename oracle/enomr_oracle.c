@@ -510,13 +510,19 @@ int orc_euler_eigen(int c, double gamma, const double *UL, const double *UR, dou
     return ORC_OK;
 }
 
-/* Per-field alpha over the interior cells of a line (reading C-8):
- * alpha_k = max_i |lambda_k(U_i)| with lambda = (u-c, u, [u], u+c). */
-static int line_alpha(int c, double gamma, long N, const double *Ul /* [N][c] */, double *alpha)
+/* Per-field alpha over the interior cells of a line (reading of
+ * Eq. LF_Flux_Split for systems): alpha_k = max_i |lambda_k(U_i)| with
+ * lambda = (u-c, u, [u], u+c).  amax (optional) receives the first cell
+ * attaining each maximum. */
+static int line_alpha(int c, double gamma, long N, const double *Ul /* [N][c] */, double *alpha,
+                      int *amax)
 {
     long i;
     int k;
-    for (k = 0; k < c; ++k) alpha[k] = 0.0;
+    for (k = 0; k < c; ++k) {
+        alpha[k] = 0.0;
+        if (amax) amax[k] = 0;
+    }
     for (i = 0; i < N; ++i) {
         prim_t P;
         double lam[4];
@@ -525,7 +531,33 @@ static int line_alpha(int c, double gamma, long N, const double *Ul /* [N][c] */
         lam[1] = P.un;
         lam[2] = (c == 4) ? P.un : P.un + P.c;
         lam[3] = P.un + P.c;
-        for (k = 0; k < c; ++k) alpha[k] = dmax(alpha[k], dabs(lam[k]));
+        for (k = 0; k < c; ++k)
+            if (dabs(lam[k]) > alpha[k]) {
+                alpha[k] = dabs(lam[k]);
+                if (amax) amax[k] = (int)i;
+            }
+    }
+    return ORC_OK;
+}
+
+/* The same alpha with the maximising cells given (frozen): alpha_k =
+ * |lambda_k(U_{amax[k]})|.  Used to differentiate the scheme with all its
+ * discrete choices held fixed. */
+static int line_alpha_frozen(int c, double gamma, const double *Ul, const int *amax,
+                             double *alpha)
+{
+    int k;
+    for (k = 0; k < c; ++k) {
+        prim_t P;
+        double lam;
+        if (primitive(c, gamma, Ul + (long)amax[k] * c, &P)) return ORC_ENONPHYS;
+        if (k == 0)
+            lam = P.un - P.c;
+        else if (k == c - 1)
+            lam = P.un + P.c;
+        else
+            lam = P.un;
+        alpha[k] = dabs(lam);
     }
     return ORC_OK;
 }
@@ -535,7 +567,8 @@ static int line_alpha(int c, double gamma, long N, const double *Ul /* [N][c] */
  * sel/win (optional) for this line: sel[side][field][N+1],
  * win[side][field][N+1][2g-1]; forced likewise. */
 static int sweep_line(int c, double gamma, const order_t *o, int bc, long N, const double *Ul,
-                      const double *alpha_in, const uint8_t *forced, uint8_t *sel_out,
+                      const double *alpha_fixed, const int *amax_in, int *amax_out,
+                      const uint8_t *forced, uint8_t *sel_out,
                       double *win_out, double *fhat, double *alpha_out, long *ntested)
 {
     int g = o->g, st, q, k, l;
@@ -544,9 +577,13 @@ static int sweep_line(int c, double gamma, const order_t *o, int bc, long N, con
     double *Ug = (double *)malloc(sizeof(double) * (N + 2 * g) * c);
     double *Fg = (double *)malloc(sizeof(double) * (N + 2 * g) * c);
     const long NI = N + 1;
-    st = alpha_in ? ORC_OK : line_alpha(c, gamma, N, Ul, alpha);
-    if (alpha_in)
-        for (k = 0; k < c; ++k) alpha[k] = alpha_in[k];
+    if (alpha_fixed) {
+        for (k = 0; k < c; ++k) alpha[k] = alpha_fixed[k];
+        st = ORC_OK;
+    } else {
+        st = amax_in ? line_alpha_frozen(c, gamma, Ul, amax_in, alpha)
+                     : line_alpha(c, gamma, N, Ul, alpha, amax_out);
+    }
     if (alpha_out)
         for (k = 0; k < c; ++k) alpha_out[k] = alpha[k];
     /* ghost fill and physical flux per cell */
@@ -622,9 +659,10 @@ static int sweep_line(int c, double gamma, const order_t *o, int bc, long N, con
 }
 
 /* 1D Euler: U is [3][N] (component-major).  sel/win as in sweep_line. */
-int orc_rhs_euler1d(long N, const double *U, double h, int R, int bc, double gamma,
-                    const uint8_t *forced, uint8_t *sel_out, double *win_out, double *rhs,
-                    double *alpha_out, long *ntested_out)
+static int rhs_euler1d(long N, const double *U, double h, int R, int bc, double gamma,
+                       const int *amax_in, int *amax_out, const uint8_t *forced,
+                       uint8_t *sel_out, double *win_out, double *rhs, double *alpha_out,
+                       long *ntested_out)
 {
     const order_t *o = get_order(R);
     double *Ul, *fhat;
@@ -637,8 +675,8 @@ int orc_rhs_euler1d(long N, const double *U, double h, int R, int bc, double gam
     fhat = (double *)malloc(sizeof(double) * (N + 1) * 3);
     for (i = 0; i < N; ++i)
         for (q = 0; q < 3; ++q) Ul[i * 3 + q] = U[q * N + i];
-    st = sweep_line(3, gamma, o, bc, N, Ul, NULL, forced, sel_out, win_out, fhat, alpha_out,
-                    &ntested);
+    st = sweep_line(3, gamma, o, bc, N, Ul, NULL, amax_in, amax_out, forced, sel_out, win_out,
+                    fhat, alpha_out, &ntested);
     if (!st)
         for (i = 0; i < N; ++i)
             for (q = 0; q < 3; ++q) rhs[q * N + i] = -(fhat[(i + 1) * 3 + q] - fhat[i * 3 + q]) / h;
@@ -648,15 +686,35 @@ int orc_rhs_euler1d(long N, const double *U, double h, int R, int bc, double gam
     return st;
 }
 
+int orc_rhs_euler1d(long N, const double *U, double h, int R, int bc, double gamma,
+                    const uint8_t *forced, uint8_t *sel_out, double *win_out, double *rhs,
+                    double *alpha_out, long *ntested_out)
+{
+    return rhs_euler1d(N, U, h, R, bc, gamma, NULL, NULL, forced, sel_out, win_out, rhs,
+                       alpha_out, ntested_out);
+}
+
+/* 1D Euler with every discrete choice given: the stencils (forced) and the
+ * cell maximising each alpha (amax[3]).  amax_out (optional) receives the
+ * maximising cells of the plain scheme when amax_in is NULL. */
+int orc_rhs_euler1d_frozen(long N, const double *U, double h, int R, int bc, double gamma,
+                           const uint8_t *forced, const int *amax_in, int *amax_out, double *rhs)
+{
+    return rhs_euler1d(N, U, h, R, bc, gamma, amax_in, amax_out, forced, NULL, NULL, rhs, NULL,
+                       NULL);
+}
+
 /* 2D Euler, dimension by dimension.  U is [4][ny][nx] with components
  * (rho, rho u, rho v, E).  rhs = x part + y part, where
  * x part = -(F_{i+1/2} - F_{i-1/2})/dx on each row and
  * y part = -(G_{j+1/2} - G_{j-1/2})/dy on each column.
  * sel/win layout: x sweep first, [side][field][row][nx+1], then the y sweep,
  * [side][field][col][ny+1]; win has a trailing [2g-1]. */
-int orc_rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, int R, int bc,
-                    double gamma, const uint8_t *forced, uint8_t *sel_out, double *win_out,
-                    double *rhs, double *alpha_x, double *alpha_y, long *ntested_out)
+static int rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, int R, int bc,
+                       double gamma, const double *afx, const double *afy,
+                       const int *amx_in, const int *amy_in, int *amx_out,
+                       int *amy_out, const uint8_t *forced, uint8_t *sel_out, double *win_out,
+                       double *rhs, double *alpha_x, double *alpha_y, long *ntested_out)
 {
     const order_t *o = get_order(R);
     const long ncell = nx * ny;
@@ -687,7 +745,9 @@ int orc_rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, int
         if (forced)
             for (r = 0; r < 8; ++r)
                 memcpy(fl + r * (nx + 1), forced + ((long)r * ny + y) * (nx + 1), nx + 1);
-        lst = sweep_line(4, gamma, o, bc, nx, Ul, NULL, fl, sl, wl, fh,
+        lst = sweep_line(4, gamma, o, bc, nx, Ul, afx ? afx + y * 4 : NULL,
+                         amx_in ? amx_in + y * 4 : NULL,
+                         amx_out ? amx_out + y * 4 : NULL, fl, sl, wl, fh,
                          alpha_x ? alpha_x + y * 4 : NULL, &nt);
         ntested += nt;
         if (lst) {
@@ -737,7 +797,9 @@ int orc_rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, int
         if (forced)
             for (r = 0; r < 8; ++r)
                 memcpy(fl + r * (ny + 1), forced + ysel_off + ((long)r * nx + x) * (ny + 1), ny + 1);
-        lst = sweep_line(4, gamma, o, bc, ny, Ul, NULL, fl, sl, wl, fh,
+        lst = sweep_line(4, gamma, o, bc, ny, Ul, afy ? afy + x * 4 : NULL,
+                         amy_in ? amy_in + x * 4 : NULL,
+                         amy_out ? amy_out + x * 4 : NULL, fl, sl, wl, fh,
                          alpha_y ? alpha_y + x * 4 : NULL, &nt);
         ntested += nt;
         if (lst) {
@@ -773,6 +835,37 @@ int orc_rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, int
     free(xpart);
     if (ntested_out) *ntested_out = ntested;
     return st;
+}
+
+int orc_rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, int R, int bc,
+                    double gamma, const uint8_t *forced, uint8_t *sel_out, double *win_out,
+                    double *rhs, double *alpha_x, double *alpha_y, long *ntested_out)
+{
+    return rhs_euler2d(nx, ny, U, dx, dy, R, bc, gamma, NULL, NULL, NULL, NULL, NULL, NULL, forced,
+                       sel_out, win_out, rhs, alpha_x, alpha_y, ntested_out);
+}
+
+/* 2D Euler with every discrete choice given (stencils and, per row and per
+ * column, the cell maximising each field's alpha: amx[ny][4], amy[nx][4]);
+ * with amx_in NULL the plain scheme runs and its maximising cells are
+ * written to amx_out/amy_out. */
+int orc_rhs_euler2d_frozen(long nx, long ny, const double *U, double dx, double dy, int R, int bc,
+                           double gamma, const uint8_t *forced, const int *amx_in,
+                           const int *amy_in, int *amx_out, int *amy_out, double *rhs)
+{
+    return rhs_euler2d(nx, ny, U, dx, dy, R, bc, gamma, NULL, NULL, amx_in, amy_in, amx_out,
+                       amy_out, forced, NULL, NULL, rhs, NULL, NULL, NULL);
+}
+
+/* 2D Euler with the stencils forced and the split speeds given as values
+ * (alpha_x[ny][4], alpha_y[nx][4]): used to differentiate with respect to
+ * alpha alone. */
+int orc_rhs_euler2d_alpha(long nx, long ny, const double *U, double dx, double dy, int R, int bc,
+                          double gamma, const uint8_t *forced, const double *alpha_x,
+                          const double *alpha_y, double *rhs)
+{
+    return rhs_euler2d(nx, ny, U, dx, dy, R, bc, gamma, alpha_x, alpha_y, NULL, NULL, NULL, NULL,
+                       forced, NULL, NULL, rhs, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------- */

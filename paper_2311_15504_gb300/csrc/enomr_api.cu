@@ -26,6 +26,10 @@ struct enomr_ctx {
     double *U1, *U2;   // SSP-RK3 stage buffers
     double *D;         // 2D: x-sweep partial RHS
     long long nstate;  // doubles in one state
+    // adjoint scratch: argmax cell of each alpha, alpha cotangents, stage cotangents
+    unsigned long long *ix, *iy;
+    double *axb, *ayb;
+    double *Ub1, *Ub2;
     // optional per-kernel event timing (enomr_profile_begin/end)
     int prof_kernel, prof_max, prof_n;
     cudaEvent_t *prof_ev;
@@ -71,19 +75,19 @@ __global__ void __launch_bounds__(256) k_alpha(AlphaArgs A)
                                                (C == 4) ? A.U[2 * ncell + i] : 0.0,
                                                A.U[(C - 1) * ncell + i], A.gm1, A.gamma, A.status);
             const double u = cw.u, v = cw.v, c = cw.c;
-            rm[0] = __double_as_longlong(fabs(u - c));
+            rm[0] = __double_as_longlong(fabs(__dsub_rn(u, c)));
             rm[1] = __double_as_longlong(fabs(u));
-            rm[2] = __double_as_longlong(fabs(u + c));
+            rm[2] = __double_as_longlong(fabs(__dadd_rn(u, c)));
             if (C == 4) {
-                unsigned long long y0 = __double_as_longlong(fabs(v - c));
+                unsigned long long y0 = __double_as_longlong(fabs(__dsub_rn(v, c)));
                 unsigned long long y1 = __double_as_longlong(fabs(v));
-                unsigned long long y2 = __double_as_longlong(fabs(v + c));
+                unsigned long long y2 = __double_as_longlong(fabs(__dadd_rn(v, c)));
                 cm[0] = cm[0] > y0 ? cm[0] : y0;
                 cm[1] = cm[1] > y1 ? cm[1] : y1;
                 cm[2] = cm[2] > y2 ? cm[2] : y2;
             }
-            double s = (fabs(u) + c) * A.inv_dx;
-            if (C == 4) s = fma(fabs(v) + c, A.inv_dy, s);
+            double s = __dmul_rn(__dadd_rn(fabs(u), c), A.inv_dx);
+            if (C == 4) s = __fma_rn(__dadd_rn(fabs(v), c), A.inv_dy, s);
             unsigned long long sb = __double_as_longlong(s);
             smx = smx > sb ? smx : sb;
         }
@@ -123,6 +127,83 @@ __global__ void __launch_bounds__(256) k_alpha(AlphaArgs A)
         for (int j = 1; j < 8; ++j) m = m > sred[j] ? m : sred[j];
         atomicMax((unsigned long long *)A.smax, m);
     }
+}
+
+// First cell (smallest index along its line) whose wave speed equals the
+// line's alpha bit for bit: the frozen argmax of the adjoint.
+template <int C>
+__global__ void __launch_bounds__(256) k_alpha_argmax(AlphaArgs A, unsigned long long *ix,
+                                                     unsigned long long *iy)
+{
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const long long x = (long long)blockIdx.x * 32 + tx;
+    const long long ncell = A.nx * A.ny;
+    for (int r = 0; r < 4; ++r) {
+        const long long y = (long long)blockIdx.y * 32 + ty + 8 * r;
+        if (x >= A.nx || y >= A.ny) continue;
+        const long long i = y * A.nx + x;
+        const CellWaves cw = cell_waves<C>(A.U[i], A.U[ncell + i], (C == 4) ? A.U[2 * ncell + i] : 0.0,
+                                           A.U[(C - 1) * ncell + i], A.gm1, A.gamma, A.status);
+        const double sx[3] = {fabs(__dsub_rn(cw.u, cw.c)), fabs(cw.u), fabs(__dadd_rn(cw.u, cw.c))};
+        for (int k = 0; k < 3; ++k)
+            if (__double_as_longlong(sx[k]) == __double_as_longlong(A.ax[3 * y + k]))
+                atomicMin(ix + 3 * y + k, (unsigned long long)x);
+        if (C == 4) {
+            const double sy[3] = {fabs(__dsub_rn(cw.v, cw.c)), fabs(cw.v), fabs(__dadd_rn(cw.v, cw.c))};
+            for (int k = 0; k < 3; ++k)
+                if (__double_as_longlong(sy[k]) == __double_as_longlong(A.ay[3 * x + k]))
+                    atomicMin(iy + 3 * x + k, (unsigned long long)y);
+        }
+    }
+}
+
+// alpha_k = |lambda_k(U_a)| at the frozen argmax cell a: add
+// alpha_bar * sign(lambda_k) * d lambda_k / dU to Ubar(a).  One thread per
+// (line, k); lines 0..ny-1 are rows (x sweep), then nx columns (y sweep).
+template <int C>
+__global__ void k_alpha_vjp(const double *U, long long nx, long long ny, double gm1, double gamma,
+                            const unsigned long long *ix, const unsigned long long *iy,
+                            const double *axb, const double *ayb, double *Ubar)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nl = (C == 4) ? ny + nx : ny;
+    if (t >= 3 * nl) return;
+    const long long line = t / 3;
+    const int k = (int)(t - 3 * line);
+    const bool ysw = line >= ny;
+    const double ab = ysw ? ayb[3 * (line - ny) + k] : axb[3 * line + k];
+    const unsigned long long a = ysw ? iy[3 * (line - ny) + k] : ix[3 * line + k];
+    if (ab == 0.0 || a == ~0ULL) return;
+    const long long ncell = nx * ny;
+    const long long i = ysw ? (long long)a * nx + (line - ny) : line * nx + (long long)a;
+    const int qn = ysw ? 2 : 1, qt = ysw ? 1 : 2;
+    const double rho = U[i], mn = U[qn * ncell + i], E = U[(C - 1) * ncell + i];
+    const double mt = (C == 4) ? U[qt * ncell + i] : 0.0;
+    const double ir = 1.0 / rho;
+    const double un = mn * ir, ut = mt * ir;
+    const double p = gm1 * (E - 0.5 * rho * (un * un + ut * ut));
+    const double c = sqrt(gamma * p * ir);
+    const double lam = (k == 0) ? un - c : ((k == 1) ? un : un + c);
+    const double lb = (lam > 0.0) ? ab : ((lam < 0.0) ? -ab : 0.0);
+    const double un_b = lb;
+    const double c_b = (k == 0) ? -lb : ((k == 2) ? lb : 0.0);
+    const double p_b = c_b * gamma * ir / (2.0 * c);
+    double r_b = -c_b * c * ir * 0.5 - un_b * un * ir + p_b * 0.5 * gm1 * (un * un + ut * ut);
+    const double mn_b = un_b * ir - p_b * gm1 * un;
+    const double mt_b = -p_b * gm1 * ut;
+    const double E_b = p_b * gm1;
+    atomicAdd(Ubar + i, r_b);
+    atomicAdd(Ubar + qn * ncell + i, mn_b);
+    if (C == 4) atomicAdd(Ubar + qt * ncell + i, mt_b);
+    atomicAdd(Ubar + (C - 1) * ncell + i, E_b);
+}
+
+// y = a x (+ y if acc)
+__global__ void k_axpy(long long n, double a, const double *x, double *y, int acc)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = acc ? fma(a, x[i], y[i]) : a * x[i];
 }
 
 __global__ void k_set_dt(const double *smax, double cfl, double dt_fixed, double *dt)
@@ -178,6 +259,19 @@ template <int R> struct E2XF {
 };
 template <int R> struct E2YF {
     static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler2d_y<R>(a, s); }
+};
+
+template <int R> struct VjpF {
+    static cudaError_t run(const VjpArgs &a, int C, int dir, cudaStream_t s)
+    {
+        return launch_sweep_vjp<R>(a, C, dir, s);
+    }
+};
+template <int R> struct AdvVjpF {
+    static cudaError_t run(const AdvArgs &a, const double *Lb, double *Ub, double sc, cudaStream_t s)
+    {
+        return launch_advection_vjp<R>(a, Lb, Ub, sc, s);
+    }
 };
 
 static enomr_status cu(cudaError_t e) { return e == cudaSuccess ? ENOMR_OK : ENOMR_ECUDA; }
@@ -316,6 +410,12 @@ ENOMR_API void enomr_free(enomr_ctx *c)
     cudaFree(c->U1);
     cudaFree(c->U2);
     cudaFree(c->D);
+    cudaFree(c->ix);
+    cudaFree(c->iy);
+    cudaFree(c->axb);
+    cudaFree(c->ayb);
+    cudaFree(c->Ub1);
+    cudaFree(c->Ub2);
     if (c->prof_ev) {
         for (int i = 0; i < 2 * c->prof_max; ++i) cudaEventDestroy(c->prof_ev[i]);
         free(c->prof_ev);
@@ -366,7 +466,13 @@ ENOMR_API enomr_status enomr_init(enomr_ctx **out, int eq, int ndim, int64_t nx,
               cudaMalloc(&c->status, sizeof(int)) == cudaSuccess &&
               cudaMalloc(&c->U1, sizeof(double) * c->nstate) == cudaSuccess &&
               cudaMalloc(&c->U2, sizeof(double) * c->nstate) == cudaSuccess &&
-              (ndim == 1 || cudaMalloc(&c->D, sizeof(double) * c->nstate) == cudaSuccess);
+              (ndim == 1 || cudaMalloc(&c->D, sizeof(double) * c->nstate) == cudaSuccess) &&
+              cudaMalloc(&c->ix, sizeof(unsigned long long) * 3 * ny) == cudaSuccess &&
+              cudaMalloc(&c->iy, sizeof(unsigned long long) * 3 * nx) == cudaSuccess &&
+              cudaMalloc(&c->axb, sizeof(double) * 3 * ny) == cudaSuccess &&
+              cudaMalloc(&c->ayb, sizeof(double) * 3 * nx) == cudaSuccess &&
+              cudaMalloc(&c->Ub1, sizeof(double) * c->nstate) == cudaSuccess &&
+              cudaMalloc(&c->Ub2, sizeof(double) * c->nstate) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         enomr_free(c);
@@ -491,6 +597,132 @@ ENOMR_API enomr_status enomr_get_status(enomr_ctx *c)
     CU_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
     return h ? ENOMR_ENONPHYS : ENOMR_OK;
+}
+
+static enomr_status rhs_vjp_impl(enomr_ctx *c, const double *U, const double *Lbar, double *Ubar,
+                                 double scale)
+{
+    if (c->eq == ENOMR_ADVECTION) {
+        AdvArgs a;
+        memset(&a, 0, sizeof(a));
+        a.U = U;
+        a.n = c->nx;
+        a.bc = c->bc;
+        a.a = c->adv;
+        a.inv_h = 1.0 / c->dx;
+        return cu(by_order<AdvVjpF>(c->order, a, Lbar, Ubar, scale, c->stream));
+    }
+    const int C = c->ndim == 2 ? 4 : 3;
+    enomr_status st = compute_alpha(c, U, false);
+    if (st) return st;
+    CU_TRY(cudaMemsetAsync(c->ix, 0xff, sizeof(unsigned long long) * 3 * c->ny, c->stream));
+    CU_TRY(cudaMemsetAsync(c->iy, 0xff, sizeof(unsigned long long) * 3 * c->nx, c->stream));
+    CU_TRY(cudaMemsetAsync(c->axb, 0, sizeof(double) * 3 * c->ny, c->stream));
+    CU_TRY(cudaMemsetAsync(c->ayb, 0, sizeof(double) * 3 * c->nx, c->stream));
+    AlphaArgs aa;
+    memset(&aa, 0, sizeof(aa));
+    aa.U = U;
+    aa.nx = c->nx;
+    aa.ny = c->ny;
+    aa.gm1 = c->gamma - 1.0;
+    aa.gamma = c->gamma;
+    aa.ax = c->ax;
+    aa.ay = c->ay;
+    aa.status = c->status;
+    dim3 grid((unsigned)((c->nx + 31) / 32), (unsigned)((c->ny + 31) / 32));
+    if (C == 4)
+        k_alpha_argmax<4><<<grid, 256, 0, c->stream>>>(aa, c->ix, c->iy);
+    else
+        k_alpha_argmax<3><<<grid, 256, 0, c->stream>>>(aa, c->ix, c->iy);
+    CU_TRY(cudaGetLastError());
+    VjpArgs v;
+    v.U = U;
+    v.Lbar = Lbar;
+    v.Ubar = Ubar;
+    v.nx = c->nx;
+    v.ny = c->ny;
+    v.bc = c->bc;
+    v.gm1 = c->gamma - 1.0;
+    v.inv_gm1 = 1.0 / (c->gamma - 1.0);
+    v.gamma = c->gamma;
+    v.scale = scale;
+    v.status = c->status;
+    v.inv_h = 1.0 / c->dx;
+    v.alpha = c->ax;
+    v.alpha_bar = c->axb;
+    CU_TRY(by_order<VjpF>(c->order, v, C, 0, c->stream));
+    if (C == 4) {
+        v.inv_h = 1.0 / c->dy;
+        v.alpha = c->ay;
+        v.alpha_bar = c->ayb;
+        CU_TRY(by_order<VjpF>(c->order, v, C, 1, c->stream));
+    }
+    const long long nl = (C == 4) ? c->ny + c->nx : c->ny;
+    const unsigned blocks = (unsigned)((3 * nl + 255) / 256);
+    if (C == 4)
+        k_alpha_vjp<4><<<blocks, 256, 0, c->stream>>>(U, c->nx, c->ny, c->gamma - 1.0, c->gamma,
+                                                      c->ix, c->iy, c->axb, c->ayb, Ubar);
+    else
+        k_alpha_vjp<3><<<blocks, 256, 0, c->stream>>>(U, c->nx, c->ny, c->gamma - 1.0, c->gamma,
+                                                      c->ix, c->iy, c->axb, c->ayb, Ubar);
+    return cu(cudaGetLastError());
+}
+
+static enomr_status axpy(enomr_ctx *c, double a, const double *x, double *y, int acc)
+{
+    k_axpy<<<1216, 256, 0, c->stream>>>(c->nstate, a, x, y, acc);
+    return cu(cudaGetLastError());
+}
+
+ENOMR_API enomr_status enomr_rhs_vjp(enomr_ctx *c, const double *U, const double *Lbar,
+                                     double *Ubar, double scale, int accumulate)
+{
+    if (!c || !U || !Lbar || !Ubar || (const double *)Ubar == U || (const double *)Ubar == Lbar)
+        return ENOMR_EINVAL;
+    if (!accumulate) CU_TRY(cudaMemsetAsync(Ubar, 0, sizeof(double) * c->nstate, c->stream));
+    return rhs_vjp_impl(c, U, Lbar, Ubar, scale);
+}
+
+ENOMR_API enomr_status enomr_step_vjp(enomr_ctx *c, const double *Un, double dt,
+                                      const double *Ubar_np1, double *Ubar_n)
+{
+    if (!c || !Un || !Ubar_np1 || !Ubar_n || !(dt > 0.0)) return ENOMR_EINVAL;
+    if ((const double *)Ubar_n == Ubar_np1 || (const double *)Ubar_n == Un) return ENOMR_EINVAL;
+    enomr_status st;
+    // recompute the stages from the step's checkpoint U^n
+    CU_TRY(launch_set_dt(c->smax, 0.0, dt, c->dt, c->stream));
+    if ((st = stage_impl(c, 1, Un, Un, c->U1))) return st;
+    if ((st = stage_impl(c, 2, Un, c->U1, c->U2))) return st;
+    // U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2))
+    if ((st = axpy(c, 1.0 / 3.0, Ubar_np1, Ubar_n, 0))) return st;
+    if ((st = axpy(c, 2.0 / 3.0, Ubar_np1, c->Ub2, 0))) return st;
+    if ((st = rhs_vjp_impl(c, c->U2, Ubar_np1, c->Ub2, 2.0 / 3.0 * dt))) return st;
+    // U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
+    if ((st = axpy(c, 0.75, c->Ub2, Ubar_n, 1))) return st;
+    if ((st = axpy(c, 0.25, c->Ub2, c->Ub1, 0))) return st;
+    if ((st = rhs_vjp_impl(c, c->U1, c->Ub2, c->Ub1, 0.25 * dt))) return st;
+    // U1 = U^n + dt L(U^n)
+    if ((st = axpy(c, 1.0, c->Ub1, Ubar_n, 1))) return st;
+    return rhs_vjp_impl(c, Un, c->Ub1, Ubar_n, dt);
+}
+
+ENOMR_API enomr_status enomr_debug_alpha(enomr_ctx *c, double *alpha_x, double *alpha_y,
+                                         double *alpha_bar_x, double *alpha_bar_y,
+                                         uint64_t *argmax_x, uint64_t *argmax_y)
+{
+    if (!c) return ENOMR_EINVAL;
+    const size_t bx = sizeof(double) * 3 * c->ny, by = sizeof(double) * 3 * c->nx;
+    if (argmax_x) CU_TRY(cudaMemcpyAsync(argmax_x, c->ix, bx, cudaMemcpyDeviceToDevice, c->stream));
+    if (argmax_y && c->ndim == 2)
+        CU_TRY(cudaMemcpyAsync(argmax_y, c->iy, by, cudaMemcpyDeviceToDevice, c->stream));
+    if (alpha_x) CU_TRY(cudaMemcpyAsync(alpha_x, c->ax, bx, cudaMemcpyDeviceToDevice, c->stream));
+    if (alpha_y && c->ndim == 2)
+        CU_TRY(cudaMemcpyAsync(alpha_y, c->ay, by, cudaMemcpyDeviceToDevice, c->stream));
+    if (alpha_bar_x)
+        CU_TRY(cudaMemcpyAsync(alpha_bar_x, c->axb, bx, cudaMemcpyDeviceToDevice, c->stream));
+    if (alpha_bar_y && c->ndim == 2)
+        CU_TRY(cudaMemcpyAsync(alpha_bar_y, c->ayb, by, cudaMemcpyDeviceToDevice, c->stream));
+    return ENOMR_OK;
 }
 
 ENOMR_API enomr_status enomr_profile_begin(enomr_ctx *c, int kernel, int max_launches)

@@ -92,7 +92,7 @@ __global__ void k_batch_dt(const double *alpha, const double *inv_dx, double cfl
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < nprob) {
         const double a0 = alpha[3 * p], a2 = alpha[3 * p + 2];
-        const double smax = (a0 > a2 ? a0 : a2) * inv_dx[p];
+        const double smax = __dmul_rn(a0 > a2 ? a0 : a2, inv_dx[p]);
         dt[p] = cfl / smax;
     }
 }

@@ -103,6 +103,23 @@ template <int R> cudaError_t launch_euler1d(const SweepArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, cudaStream_t s);
 
+// Transpose-Jacobian product of one sweep (enomr_vjp.cuh).
+struct VjpArgs {
+    const double *U;      // stage state [C][ny][nx]
+    const double *Lbar;   // cotangent of L(U), same layout
+    double *Ubar;         // output, accumulated with atomicAdd
+    long long nx, ny;
+    int bc;
+    double gm1, inv_gm1, gamma, inv_h, scale;
+    const double *alpha;  // [lines][3]
+    double *alpha_bar;    // [lines][3], accumulated
+    int *status;
+};
+
+template <int R> cudaError_t launch_sweep_vjp(const VjpArgs &a, int C, int dir, cudaStream_t s);
+template <int R> cudaError_t launch_advection_vjp(const AdvArgs &a, const double *Lbar,
+                                                  double *Ubar, double scale, cudaStream_t s);
+
 cudaError_t launch_alpha(int C, const AlphaArgs &a, cudaStream_t s);
 cudaError_t launch_set_dt(const double *smax, double cfl, double dt_fixed, double *dt_dev,
                           cudaStream_t s);

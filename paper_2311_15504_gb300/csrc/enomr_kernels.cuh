@@ -249,26 +249,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
         double u[C];
 #pragma unroll
         for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
-        const double rho = u[0];
-        const double rr = rsqrt(rho);  // 1/sqrt(rho): gives sqrt(rho) and 1/rho
-        const double ir = rr * rr;
-        const double un = u[QN] * ir;
-        const double ut = (C == 4) ? u[QT] * ir : 0.0;
-        const double E = u[C - 1];
-        const double p = A.gm1 * (E - 0.5 * rho * (un * un + ut * ut));
-        if (!(rho > 0.0) || !(p > 0.0) || !(fabs(E) < 1e300)) atomicOr(A.status, ST_NONPHYS_CELL);
+        const StagedCell<C> sc_ = stage_cell<C>(u[0], u[QN], (C == 4) ? u[QT] : 0.0, u[C - 1], A.gm1);
+        if (!(u[0] > 0.0) || !(sc_.p > 0.0) || !(fabs(u[C - 1]) < 1e300))
+            atomicOr(A.status, ST_NONPHYS_CELL);
         sU[0][line][s] = u[0];
         sU[1][line][s] = u[QN];
         if (C == 4) sU[2][line][s] = u[QT];
-        sU[C - 1][line][s] = E;
-        sF[0][line][s] = u[QN];
-        sF[1][line][s] = fma(u[QN], un, p);
-        if (C == 4) sF[2][line][s] = u[QT] * un;
-        sF[C - 1][line][s] = (E + p) * un;
-        sP[0][line][s] = rho * rr;
-        sP[1][line][s] = un;
-        sP[2][line][s] = ut;
-        sP[3][line][s] = (E + p) * ir;
+        sU[C - 1][line][s] = u[C - 1];
+#pragma unroll
+        for (int q = 0; q < C; ++q) sF[q][line][s] = sc_.F[q];
+        sP[0][line][s] = sc_.sq;
+        sP[1][line][s] = sc_.un;
+        sP[2][line][s] = sc_.ut;
+        sP[3][line][s] = sc_.H;
     }
     __syncthreads();
 
@@ -291,26 +284,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
 #pragma unroll
     for (int q = 0; q < C; ++q)
         eqLR = eqLR && (__double_as_longlong(sU[q][line][sl]) == __double_as_longlong(sU[q][line][sr]));
-    double uh, vh, Hh;
-    if (eqLR) {
-        uh = sP[1][line][sl];
-        vh = (C == 4) ? sP[2][line][sl] : 0.0;
-        Hh = sP[3][line][sl];
-    } else {
-        const double qL = sP[0][line][sl], qR = sP[0][line][sr];
-        const double rs = 1.0 / (qL + qR);
-        uh = (qL * sP[1][line][sl] + qR * sP[1][line][sr]) * rs;
-        vh = (C == 4) ? (qL * sP[2][line][sl] + qR * sP[2][line][sr]) * rs : 0.0;
-        Hh = (qL * sP[3][line][sl] + qR * sP[3][line][sr]) * rs;
-    }
-    const double hq = 0.5 * (uh * uh + vh * vh);
-    const double c2 = A.gm1 * (Hh - hq);
-    if (valid && !(c2 > 0.0)) atomicOr(A.status, ST_NONPHYS_ROE);
-    const double ic = rsqrt(c2);         // 1/c: one reciprocal square root
-    const double cs = c2 * ic;           // c
-    const double kap = cs * A.inv_gm1;   // c / (gamma-1)
-    const double c2g = c2 * A.inv_gm1;   // c^2 / (gamma-1)
-    const double b1 = A.gm1 * (ic * ic);  // (gamma-1) / c^2
+    const RoeFace rf = roe_face(eqLR, sP[0][line][sl], sP[1][line][sl], sP[2][line][sl],
+                                sP[3][line][sl], sP[0][line][sr], sP[1][line][sr],
+                                sP[2][line][sr], sP[3][line][sr], C == 4, A.gm1, A.inv_gm1);
+    if (valid && !(rf.c2 > 0.0)) atomicOr(A.status, ST_NONPHYS_ROE);
+    const double uh = rf.uh, vh = rf.vh, Hh = rf.Hh, hq = rf.hq, cs = rf.cs, kap = rf.kap,
+                 c2g = rf.c2g, b1 = rf.b1;
 
     const double *al = A.alpha + 3 * (Lg < nlines ? Lg : nlines - 1);
     const double a_m = al[0], a_0 = al[1], a_p = al[2];

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "enomr_kernels.cuh"
+#include "enomr_vjp.cuh"
 
 namespace enomr {
 
@@ -65,5 +66,37 @@ template <int R> cudaError_t launch_batch_stage(const BatchArgs &a, int tp, int 
 }
 
 template cudaError_t launch_batch_stage<ENOMR_R>(const BatchArgs &, int, int, cudaStream_t);
+
+}  // namespace enomr
+
+namespace enomr {
+
+template <int R> cudaError_t launch_sweep_vjp(const VjpArgs &a, int C, int dir, cudaStream_t s)
+{
+    if (C == 3) {
+        const long long tiles = (a.nx + 62) / 63;
+        k_sweep_vjp<R, 3, 0, 64, 1><<<dim3((unsigned)tiles, 1), 64, 0, s>>>(a);
+    } else if (dir == 0) {
+        const long long tx = (a.nx + 62) / 63;
+        k_sweep_vjp<R, 4, 0, 64, 1><<<dim3((unsigned)tx, (unsigned)a.ny), 64, 0, s>>>(a);
+    } else {
+        const long long tx = (a.nx + 1) / 2;
+        const long long ty = (a.ny + 30) / 31;
+        k_sweep_vjp<R, 4, 1, 32, 2><<<dim3((unsigned)tx, (unsigned)ty), 64, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t launch_advection_vjp(const AdvArgs &a, const double *Lbar, double *Ubar,
+                                                  double scale, cudaStream_t s)
+{
+    const long long tiles = (a.n + ADV_TP - 2) / (ADV_TP - 1);
+    k_advection_vjp<R, ADV_TP><<<(unsigned)tiles, ADV_TP, 0, s>>>(a, Lbar, Ubar, scale);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_sweep_vjp<ENOMR_R>(const VjpArgs &, int, int, cudaStream_t);
+template cudaError_t launch_advection_vjp<ENOMR_R>(const AdvArgs &, const double *, double *, double,
+                                                   cudaStream_t);
 
 }  // namespace enomr

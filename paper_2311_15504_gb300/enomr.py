@@ -44,6 +44,9 @@ _SIGS = {
     "enomr_probe_fp64_fma": (_I, [_P, ctypes.c_int64, _P, ctypes.POINTER(_D),
                                  ctypes.POINTER(_D)]),
     "enomr_rhs_euler2d_noalloc": (_I, [_P, _P, _L, _L, _D, _D, _I, _D, _I, _P]),
+    "enomr_rhs_vjp": (_I, [_P, _P, _P, _P, _D, _I]),
+    "enomr_step_vjp": (_I, [_P, _P, _D, _P, _P]),
+    "enomr_debug_alpha": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "enomr_batch_init": (_I, [ctypes.POINTER(_P), _L, _P, _P, _I, _D, _I, _P]),
     "enomr_batch_free": (None, [_P]),
     "enomr_batch_set_stream": (_I, [_P, _P]),
@@ -178,6 +181,41 @@ class Solver:
                "enomr_debug_selection")
         return sel
 
+    def rhs_vjp(self, U, Lbar, out=None, scale=1.0, accumulate=False):
+        """scale * J(U)^T Lbar with the forward choices at U frozen."""
+        if out is None:
+            out = torch.zeros_like(U)
+            accumulate = True
+        self._stream()
+        _check(_lib.enomr_rhs_vjp(self._ctx, self._state(U), self._state(Lbar, "Lbar"),
+                                  self._state(out, "out"), float(scale), int(accumulate)),
+               "enomr_rhs_vjp")
+        return out
+
+    def debug_alpha(self):
+        """(alpha_x, alpha_y, alpha_bar_x, alpha_bar_y, argmax_x, argmax_y) of the
+        last calls (see enomr_debug_alpha)."""
+        ax = torch.empty(self.ny, 3, dtype=torch.float64, device=self.device)
+        ay = torch.empty(self.nx, 3, dtype=torch.float64, device=self.device)
+        bx, by = torch.empty_like(ax), torch.empty_like(ay)
+        ix = torch.empty(self.ny, 3, dtype=torch.int64, device=self.device)
+        iy = torch.empty(self.nx, 3, dtype=torch.int64, device=self.device)
+        self._stream()
+        _check(_lib.enomr_debug_alpha(self._ctx, _P(ax.data_ptr()), _P(ay.data_ptr()),
+                                      _P(bx.data_ptr()), _P(by.data_ptr()), _P(ix.data_ptr()),
+                                      _P(iy.data_ptr())), "enomr_debug_alpha")
+        return ax, ay, bx, by, ix, iy
+
+    def step_vjp(self, Un, dt, Ubar_np1, out=None):
+        """(dU_{n+1}/dU_n)^T Ubar_np1 for one SSP-RK3 step of size dt from Un."""
+        if out is None:
+            out = torch.empty_like(Un)
+        self._stream()
+        _check(_lib.enomr_step_vjp(self._ctx, self._state(Un), float(dt),
+                                   self._state(Ubar_np1, "Ubar_np1"), self._state(out, "out")),
+               "enomr_step_vjp")
+        return out
+
     def profile_begin(self, kernel: int, max_launches: int):
         """Time the next launches of one kernel (1 x sweep, 2 y sweep, 3 alpha)."""
         _check(_lib.enomr_profile_begin(self._ctx, kernel, max_launches), "enomr_profile_begin")
@@ -265,3 +303,33 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class _Rollout(torch.autograd.Function):
+    """n SSP-RK3 steps with per-step checkpoints; backward runs enomr_step_vjp
+    step by step in reverse, recomputing the stages from each checkpoint."""
+
+    @staticmethod
+    def forward(ctx, U0, solver, nsteps, cfl, dt):
+        U = U0.detach().clone()
+        ckpt, dts = [], []
+        for _ in range(nsteps):
+            ckpt.append(U.clone())
+            dts.append(solver.step(U, dt, cfl, return_dt=True))
+        ctx.solver, ctx.ckpt, ctx.dts = solver, ckpt, dts
+        return U
+
+    @staticmethod
+    def backward(ctx, gout):
+        g = gout.contiguous().clone()
+        tmp = torch.empty_like(g)
+        for Un, dt in zip(reversed(ctx.ckpt), reversed(ctx.dts)):
+            ctx.solver.step_vjp(Un, dt, g, out=tmp)
+            g, tmp = tmp, g
+        return g, None, None, None, None
+
+
+def rollout(U0, solver, nsteps, cfl=0.5, dt=0.0):
+    """Differentiable: U(t_n) after nsteps SSP-RK3 steps from U0 (CFL steps
+    when dt <= 0; the step sizes are held fixed in the gradient)."""
+    return _Rollout.apply(U0, solver, nsteps, cfl, dt)

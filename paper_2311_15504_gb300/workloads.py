@@ -147,12 +147,12 @@ def riemann2d_rp1(n: int, gamma=GAMMA):
     return out, dx, dx
 
 
-def isentropic_vortex(n: int, strength=5.0, gamma=GAMMA, L=10.0):
-    """Isentropic vortex on [0,L]^2, periodic, centre (L/2, L/2), free stream
-    (rho, u, v, p) = (1, 1, 1, 1)."""
+def isentropic_vortex(n: int, strength=5.0, gamma=GAMMA, L=10.0, centre=None):
+    """Isentropic vortex on [0,L]^2, periodic, centre (L/2, L/2) unless
+    given, free stream (rho, u, v, p) = (1, 1, 1, 1)."""
     x, h = periodic_grid(0.0, L, n)
     X, Y = np.meshgrid(x + 0.5 * h, x + 0.5 * h)
-    xc = yc = 0.5 * L
+    xc, yc = (0.5 * L, 0.5 * L) if centre is None else centre
     r2 = (X - xc) ** 2 + (Y - yc) ** 2
     du = -strength / (2 * np.pi) * np.exp(0.5 * (1 - r2)) * (Y - yc)
     dv = strength / (2 * np.pi) * np.exp(0.5 * (1 - r2)) * (X - xc)
