@@ -123,6 +123,17 @@ ENOMR_API enomr_status enomr_stage(enomr_ctx *ctx, int stage, const double *Un, 
 ENOMR_API enomr_status enomr_step(enomr_ctx *ctx, double *U, double dt, double cfl,
                                   double *dt_used);
 
+/*
+ * enomr_step_lssp -- one step of the linear SSP-RK(m, m-1) scheme of
+ * Eq. (lSSPRK), in place on U (device), with fixed dt > 0, 2 <= m <= 32:
+ *   u(0) = U;  u(s) = u(s-1) + dt/2 L(u(s-1)), s = 1..m-1;
+ *   U <- sum_{k=0}^{m-2} a_k u(k) + a_{m-1} (u(m-1) + dt/2 L(u(m-1))),
+ * with a_k = alpha_{m,k} of Eq. (lSSPRK_Coe) (alpha_{m,m-1} read as
+ * (2/m) alpha_{m-1,m-2}).  Meant for linear problems (advection), where it
+ * has order m-1; uses the context's stage buffers.
+ */
+ENOMR_API enomr_status enomr_step_lssp(enomr_ctx *ctx, double *U, double dt, int m);
+
 /* enomr_cfl_dt -- the CFL step of enomr_step for state U, returned in
  * *dt_host (host).  Synchronises the stream. */
 ENOMR_API enomr_status enomr_cfl_dt(enomr_ctx *ctx, const double *U, double cfl, double *dt_host);

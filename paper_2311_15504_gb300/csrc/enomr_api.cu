@@ -565,6 +565,69 @@ ENOMR_API enomr_status enomr_step(enomr_ctx *c, double *U, double dt, double cfl
     return ENOMR_OK;
 }
 
+static enomr_status axpy(enomr_ctx *c, double a, const double *x, double *y, int acc);
+
+// Coefficients alpha_{m,0..m-1} of the linear SSP-RK(m, m-1) family:
+// alpha_{2,*} = (0, 1); alpha_{m,k} = (2/k) alpha_{m-1,k-1} for 1 <= k <= m-2,
+// alpha_{m,m-1} = (2/m) alpha_{m-1,m-2}, alpha_{m,0} = 1 - sum_{k>=1} alpha_{m,k}.
+static void lssp_alphas(int m, double *out)
+{
+    double a[40] = {0.0, 1.0};
+    for (int mm = 3; mm <= m; ++mm) {
+        double b[40];
+        double sum = 0.0;
+        for (int k = 1; k <= mm - 2; ++k) b[k] = (2.0 / k) * a[k - 1];
+        b[mm - 1] = (2.0 / mm) * a[mm - 2];
+        for (int k = 1; k <= mm - 1; ++k) sum += b[k];
+        b[0] = 1.0 - sum;
+        for (int k = 0; k < mm; ++k) a[k] = b[k];
+    }
+    for (int k = 0; k < m; ++k) out[k] = a[k];
+}
+
+ENOMR_API enomr_status enomr_step_lssp(enomr_ctx *c, double *U, double dt, int m)
+{
+    if (!c || !U || !(dt > 0.0) || m < 2 || m > 32) return ENOMR_EINVAL;
+    double al[40];
+    lssp_alphas(m, al);
+    enomr_status st;
+    // every stage advances by dt/2: u^(s) = u^(s-1) + dt/2 L(u^(s-1))
+    CU_TRY(launch_set_dt(c->smax, 0.0, 0.5 * dt, c->dt, c->stream));
+    double *acc = c->Ub1;                      // sum_{k<=m-2} alpha_k u^(k)
+    if ((st = axpy(c, al[0], U, acc, 0))) return st;
+    const double *cur = U;
+    double *bufs[2] = {c->U1, c->U2};
+    for (int s = 1; s <= m - 1; ++s) {
+        double *next = bufs[s & 1];
+        st = compute_alpha(c, cur, false);
+        if (st) return st;
+        Epilogue e;
+        memset(&e, 0, sizeof(e));
+        e.mode = EPI_STAGE;
+        e.c0 = 0.0;
+        e.c1 = 1.0;
+        e.dt_dev = c->dt;
+        e.Un = cur;
+        e.out = next;
+        if ((st = rhs_with_epilogue(c, cur, e, nullptr))) return st;
+        if (s <= m - 2 && al[s] != 0.0)
+            if ((st = axpy(c, al[s], next, acc, 1))) return st;
+        cur = next;
+    }
+    // u^{n+1} = acc + alpha_{m-1} (u^(m-1) + dt/2 L(u^(m-1)))
+    st = compute_alpha(c, cur, false);
+    if (st) return st;
+    Epilogue e;
+    memset(&e, 0, sizeof(e));
+    e.mode = EPI_STAGE;
+    e.c0 = 1.0;
+    e.c1 = al[m - 1];
+    e.dt_dev = c->dt;
+    e.Un = acc;
+    e.out = U;
+    return rhs_with_epilogue(c, cur, e, nullptr);
+}
+
 ENOMR_API enomr_status enomr_cfl_dt(enomr_ctx *c, const double *U, double cfl, double *dt_host)
 {
     if (!c || !U || !dt_host || !(cfl > 0.0)) return ENOMR_EINVAL;

@@ -23,7 +23,7 @@ template <int C>
 __device__ __forceinline__ CellWaves cell_waves(double rho, double mx, double my, double E,
                                                 double gm1, double gamma, int *status)
 {
-    const double ir = __drcp_rn(rho);
+    const double ir = 1.0 / rho;  // IEEE division: never contracted
     const double u = __dmul_rn(mx, ir);
     const double v = (C == 4) ? __dmul_rn(my, ir) : 0.0;
     const double ke = (C == 4) ? __fma_rn(u, u, __dmul_rn(v, v)) : __dmul_rn(u, u);
@@ -94,7 +94,7 @@ __device__ __forceinline__ RoeFace roe_face(bool equal, double qL, double uL, do
         r.vh = twod ? vL : 0.0;
         r.Hh = HL;
     } else {
-        const double rs = __drcp_rn(__dadd_rn(qL, qR));
+        const double rs = 1.0 / __dadd_rn(qL, qR);
         r.uh = __dmul_rn(__fma_rn(qL, uL, __dmul_rn(qR, uR)), rs);
         r.vh = twod ? __dmul_rn(__fma_rn(qL, vL, __dmul_rn(qR, vR)), rs) : 0.0;
         r.Hh = __dmul_rn(__fma_rn(qL, HL, __dmul_rn(qR, HR)), rs);

@@ -36,6 +36,7 @@ _SIGS = {
     "enomr_stage": (_I, [_P, _I, _P, _P, _P, _D]),
     "enomr_step": (_I, [_P, _P, _D, _D, _P]),
     "enomr_cfl_dt": (_I, [_P, _P, _D, _P]),
+    "enomr_step_lssp": (_I, [_P, _P, _D, _I]),
     "enomr_debug_selection": (_I, [_P, _P, _P]),
     "enomr_get_status": (_I, [_P]),
     "enomr_num_tested": (_I, [_I]),
@@ -166,6 +167,12 @@ class Solver:
             return d.value
         _check(_lib.enomr_step(self._ctx, pu, float(dt), float(cfl), None), "enomr_step")
         return None
+
+    def step_lssp(self, U, dt, m):
+        """One linear SSP-RK(m, m-1) step of size dt, in place."""
+        self._stream()
+        _check(_lib.enomr_step_lssp(self._ctx, self._state(U), float(dt), int(m)),
+               "enomr_step_lssp")
 
     def cfl_dt(self, U, cfl=0.5):
         d = ctypes.c_double()

@@ -1,0 +1,155 @@
+"""Parity at the full sizes the benchmark runs, in the benchmark's launch
+configuration (the public API with the library's fixed tile shapes).
+
+The oracle evaluates every output here (its OpenMP loops make a 4096^2 RHS
+take seconds); values are compared with the oracle re-run on the CUDA
+path's selections, and selection flips (near-ties, see tests/parity.py)
+are counted and bounded.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from parity import assert_selection, assert_values, euler_flux_scale, euler_scale_fn
+from paper_2311_15504_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build_cuda()
+    from paper_2311_15504_gb300 import enomr
+    return enomr
+
+
+def test_riemann2d_4096_order9(E):
+    """The benchmark workload: four-quadrant Riemann problem, 4096^2,
+    order 9, transmissive; checked after two CFL steps (smeared fronts)."""
+    import torch
+    n, R = 4096, 9
+    U0, dx, dy = wl.riemann2d(n, n, seed=0)
+    s = E.Solver(E.EULER, (n, n), order=R, dx=dx, dy=dy, bc=E.TRANSMISSIVE)
+    Ud = torch.from_numpy(U0).cuda()
+    for _ in range(2):
+        s.step(Ud, 0.0, 0.5)
+    U = Ud.cpu().numpy()
+    sel = s.selection(Ud).cpu().numpy()
+    got = s.rhs(Ud).cpu().numpy()
+    s.check_status()
+    ref_sel = oracle.rhs_euler2d(U, dx, dy, R, bc=oracle.BC_TRANSMISSIVE, want_sel=True)["sel"]
+    flips = np.nonzero(ref_sel != sel)[0]
+    print(f"4096^2: selection flips {flips.size} of {sel.size}")
+    assert flips.size <= 1e-3 * sel.size
+    # classify a sample of the flips: a sweep of a line depends on that line
+    # only, so the oracle's windows come from the stacked sampled lines
+    nsx = 8 * n * (n + 1)
+    rng = np.random.Generator(np.random.PCG64(0))
+    for sweep, sub in (("x", flips[flips < nsx]), ("y", flips[flips >= nsx] - nsx)):
+        if sub.size == 0:
+            continue
+        lines = np.unique((sub // (n + 1)) % n)
+        lines = np.sort(rng.choice(lines, size=min(100, lines.size), replace=False))
+        Ul = U[:, lines, :] if sweep == "x" else U[:, :, lines]
+        o = oracle.rhs_euler2d(Ul, dx, dy, R, bc=oracle.BC_TRANSMISSIVE, want_sel=True,
+                               want_win=True)
+        L = lines.size
+        if sweep == "x":
+            gsel = sel[:nsx].reshape(2, 4, n, n + 1)[:, :, lines, :]
+            osel, win = o["sel_x"], o["win_x"]
+            X = lambda y: Ul[:, y, :].T.copy()  # noqa: E731
+            fn = euler_scale_fn(X, L, n, R, 1, lambda y: o["alpha_x"][y])
+        else:
+            gsel = sel[nsx:].reshape(2, 4, n, n + 1)[:, :, lines, :]
+            osel, win = o["sel_y"], o["win_y"]
+            X = lambda x: Ul[[0, 2, 1, 3], :, x].T.copy()  # noqa: E731
+            fn = euler_scale_fn(X, L, n, R, 1, lambda x: o["alpha_y"][x])
+        # the stacked lines' sweep equals the full problem's for those lines
+        ref_l = ref_sel[:nsx] if sweep == "x" else ref_sel[nsx:]
+        assert np.array_equal(osel, ref_l.reshape(2, 4, n, n + 1)[:, :, lines, :])
+        nflip = assert_selection(R, gsel, osel, win, f"4096^2 {sweep} sample", fn)
+        print(f"  {sweep}: {nflip} sampled flips, all near-ties")
+    forced = oracle.rhs_euler2d(U, dx, dy, R, bc=oracle.BC_TRANSMISSIVE, forced=sel)["rhs"]
+    assert_values(got, forced, euler_flux_scale(U) / dx, "4096^2 riemann")
+
+
+@pytest.mark.parametrize("R", [5, 9, 17])
+def test_advection_2p24(E, R):
+    import torch
+    N = 1 << 24
+    u, h = wl.advection_sine(N)
+    u = u + 0.5 * (np.abs(np.arange(N) - N // 3) < N // 7)  # add two jumps
+    s = E.Solver(E.ADVECTION, N, order=R, dx=h, bc=E.PERIODIC)
+    ud = torch.from_numpy(u).cuda()
+    sel = s.selection(ud).cpu().numpy()
+    got = s.rhs(ud).cpu().numpy()
+    ref = oracle.rhs_advection(u, h, R, want_sel=True)
+    flips = int((ref["sel"].reshape(-1) != sel).sum())
+    assert flips <= 1e-6 * sel.size
+    forced = oracle.rhs_advection(u, h, R, forced=sel)["rhs"]
+    assert_values(got, forced, np.abs(u).max() / h, f"advection 2^24 R={R}")
+
+
+@pytest.mark.parametrize("R", [5, 17])
+def test_euler1d_6400(E, R):
+    import torch
+    U, h = wl.shock_entropy(6400)
+    s = E.Solver(E.EULER, 6400, order=R, dx=h, bc=E.TRANSMISSIVE)
+    Ud = torch.from_numpy(U).cuda()
+    for _ in range(3):
+        s.step(Ud, 0.0, 0.5)
+    U = Ud.cpu().numpy()
+    sel = s.selection(Ud).cpu().numpy()
+    got = s.rhs(Ud).cpu().numpy()
+    ref = oracle.rhs_euler1d(U, h, R, want_sel=True, want_win=True)
+    fn = euler_scale_fn(lambda line: U.T.copy(), 1, 6400, R, 1, lambda line: ref["alpha"])
+    nflip = assert_selection(R, sel, ref["sel"], ref["win"], f"euler1d 6400 R={R}", fn)
+    print(f"euler1d 6400 R={R}: {nflip} flips, all near-ties")
+    forced = oracle.rhs_euler1d(U, h, R, forced=sel)["rhs"]
+    assert_values(got, forced, euler_flux_scale(U) / h, f"euler1d 6400 R={R}")
+
+
+def test_batch_4096_sample_vs_oracle(E):
+    """The batched workload (4096 problems, sizes log-uniform in
+    [128, 8192], order 9): one persistent-kernel step; 24 problems spread
+    over the size range against the oracle."""
+    import torch
+    sizes, Us, hs = wl.riemann_batch(4096, seed=0)
+    B = E.Batch(sizes, hs, order=9, bc=E.TRANSMISSIVE)
+    Ub = B.pack(Us)
+    B.autotune(Ub, reps=1)
+    B.step(Ub, 0.5)
+    B.check_status()
+    order = np.argsort(sizes)
+    for p in order[np.linspace(0, len(sizes) - 1, 24).astype(int)]:
+        P = oracle.Problem(oracle.EQ_EULER1D, 9, int(sizes[p]), dx=float(hs[p]),
+                           bc=oracle.BC_TRANSMISSIVE)
+        ref = P.step_ssprk3(Us[p], P.cfl_dt(Us[p], 0.5))
+        got = B.view(Ub, p).cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max(), int(p)
+
+
+def test_adjoint_vortex_512_vs_frozen_oracle(E):
+    """The adjoint workload's grid (512^2 isentropic vortex, order 9, moved
+    off the grid's symmetry axes): RHS transpose product against the
+    frozen-choice oracle."""
+    import torch
+    n, R = 512, 9
+    U, h, _ = wl.isentropic_vortex(n, centre=(5.0 + 0.37 * 10 / n, 5.0 - 0.21 * 10 / n))
+    s = E.Solver(E.EULER, (n, n), order=R, dx=h, dy=h, bc=E.PERIODIC)
+    Ud = torch.from_numpy(U).cuda()
+    sel = s.selection(Ud).cpu().numpy()
+    _, am = oracle.rhs_euler2d_frozen(U, h, h, R, sel, bc=0)
+    rng = np.random.Generator(np.random.PCG64(3))
+    d = rng.standard_normal(U.shape) * (np.abs(U) + 0.1)
+    v = rng.standard_normal(U.shape)
+    eps = 1e-6
+    jd = (oracle.rhs_euler2d_frozen(U + eps * d, h, h, R, sel, amax=am, bc=0)
+          - oracle.rhs_euler2d_frozen(U - eps * d, h, h, R, sel, amax=am, bc=0)) / (2 * eps)
+    lhs = float((v * jd).sum())
+    rhs = float((s.rhs_vjp(Ud, torch.from_numpy(v).cuda()).cpu().numpy() * d).sum())
+    assert abs(lhs - rhs) <= 1e-7 * float(np.abs(v * jd).sum()), (lhs, rhs)
