@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--cfl", type=float, default=0.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--only", choices=["adjoint", "batched"], default=None,
+                    help="run one secondary measurement alone (profiling aid)")
     return ap.parse_args()
 
 
@@ -222,7 +224,7 @@ def batched_gain(enomr, workloads, dev, a, nprob=4096, order=9, reps=5):
             "gain": ms_p / ms_b, "bitwise_identical_after_2_steps": identical}
 
 
-def adjoint_ratio(enomr, workloads, dev, n=1024, order=9, steps=10):
+def adjoint_ratio(enomr, workloads, dev, n=1024, order=9, steps=10, cfl=0.5):
     """Isentropic vortex (periodic, order 9): time of one SSP-RK3 step
     against one step of the adjoint (stage recomputation from the step's
     checkpoint, three RHS transposes, the RK transpose)."""
@@ -501,9 +503,23 @@ def main_reference(a):
     print(json.dumps(out), flush=True)
 
 
+def main_only(a):
+    import torch
+    from paper_2311_15504_gb300 import enomr, workloads
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    if a.only == "adjoint":
+        out = adjoint_ratio(enomr, workloads, dev, n=a.n, steps=a.steps)
+    else:
+        out = batched_gain(enomr, workloads, dev, a)
+    print(json.dumps({"only": a.only, **out}), flush=True)
+
+
 if __name__ == "__main__":
     args = parse()
-    if args.impl == "reference":
+    if args.only:
+        main_only(args)
+    elif args.impl == "reference":
         main_reference(args)
     else:
         main_ours(args)
