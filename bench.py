@@ -111,9 +111,12 @@ class ClockSampler:
 # algorithmic FP64 work of one sweep launch (counted per interface; an FMA is
 # two flops, an add, multiply, divide or square root one)
 # ---------------------------------------------------------------------------
-def sweep_flops(order, C, sel, n_interfaces, n_flat=0):
-    """Flops of one Euler sweep.  Every interface: the Roe average and scaled
-    eigenvectors (28) and the back-projection (C == 4: 20, C == 3: 14).
+def sweep_flops(order, C, sel, n_interfaces, n_flat=0, stage_epilogue=False):
+    """Flops of one Euler sweep.  Every interface (one per cell): the cell's
+    primitives and normal flux (18), the flux difference (2C), the stage
+    update when the sweep carries it (4C: add of the other sweep, axpy and
+    combination), the Roe average and scaled eigenvectors (28) and the
+    back-projection (C == 4: 20, C == 3: 14).
     Interfaces whose two sides have flat windows (three equal cell states at
     the side's centre: IS_0 = 0 exactly, minmod returns v(0)) add only the
     projection of their two centre cells (40 flops per cell for C = 4, 24 for
@@ -129,7 +132,7 @@ def sweep_flops(order, C, sel, n_interfaces, n_flat=0):
     T = oracle.num_tested(order)
     sizes = [oracle.candidate(order, t)[0] + oracle.candidate(order, t)[1] + 1 for t in range(T)]
     cell = 40 if C == 4 else 24
-    fixed = 28 + (20 if C == 4 else 14)
+    fixed = 18 + 2 * C + (4 * C if stage_epilogue else 0) + 28 + (20 if C == 4 else 14)
     full = fixed + cell * 2 * g + C * 2 * 2 * (2 * g - 1)
     flat = fixed + cell * 2 + C * 2 * 2 + C
     flops = float(n_flat) * flat + float(n_interfaces - n_flat) * full
@@ -329,7 +332,7 @@ def main_ours(a):
         fx_flat = flat_interfaces(U, 0)
         fy_flat = flat_interfaces(U, 1)
         fl_x = sweep_flops(R, 4, hx, n * (n + 1), fx_flat)
-        fl_y = sweep_flops(R, 4, hy, n * (n + 1), fy_flat)
+        fl_y = sweep_flops(R, 4, hy, n * (n + 1), fy_flat, stage_epilogue=True)
         extras["flat_interface_fraction"] = [fx_flat / (n * (n + 1)), fy_flat / (n * (n + 1))]
         probe, _ = enomr.probe_fp64_fma(iters=20000, device=dev)
         sms = torch.cuda.get_device_properties(dev).multi_processor_count

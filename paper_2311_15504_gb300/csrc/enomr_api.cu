@@ -30,6 +30,10 @@ struct enomr_ctx {
     unsigned long long *ix, *iy;
     double *axb, *ayb;
     double *Ub1, *Ub2;
+    // forward data of the recomputed stages U^n and U^(1) for the adjoint
+    uint8_t *fsel[2];
+    double *fft[2];
+    long long nsel, nft;
     // optional per-kernel event timing (enomr_profile_begin/end)
     int prof_kernel, prof_max, prof_n;
     cudaEvent_t *prof_ev;
@@ -324,6 +328,7 @@ static SweepArgs sweep_args(enomr_ctx *c, const double *U, bool ysweep)
     a.alpha = ysweep ? c->ay : c->ax;
     a.alpha_next = nullptr;
     a.sel = nullptr;
+    a.ft_out = nullptr;
     a.status = c->status;
     memset(&a.epi, 0, sizeof(a.epi));
     return a;
@@ -331,7 +336,7 @@ static SweepArgs sweep_args(enomr_ctx *c, const double *U, bool ysweep)
 
 // Evaluate L(U) into the epilogue.  The alpha of U must be current.
 static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilogue &epi,
-                                      uint8_t *sel)
+                                      uint8_t *sel, double *ft = nullptr)
 {
     if (c->eq == ENOMR_ADVECTION) {
         AdvArgs a;
@@ -350,6 +355,7 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     if (c->ndim == 1) {
         SweepArgs a = sweep_args(c, U, false);
         a.sel = sel;
+        a.ft_out = ft;
         a.epi = epi;
         prof_start(c, 1);
         cudaError_t e = by_order<E1F>(c->order, a, c->stream);
@@ -359,6 +365,7 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     // 2D: x sweep -> D, y sweep adds D and applies the epilogue
     SweepArgs ax = sweep_args(c, U, false);
     ax.sel = sel;
+    ax.ft_out = ft;
     ax.epi.mode = EPI_STORE;
     ax.epi.out = c->D;
     prof_start(c, 1);
@@ -367,6 +374,7 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     CU_TRY(e);
     SweepArgs ay = sweep_args(c, U, true);
     ay.sel = sel ? sel + 8LL * c->ny * (c->nx + 1) : nullptr;
+    ay.ft_out = ft ? ft + 4LL * c->ny * (c->nx + 1) : nullptr;
     ay.epi = epi;
     ay.epi.Dprev = c->D;
     prof_start(c, 2);
@@ -416,6 +424,10 @@ ENOMR_API void enomr_free(enomr_ctx *c)
     cudaFree(c->ayb);
     cudaFree(c->Ub1);
     cudaFree(c->Ub2);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(c->fsel[i]);
+        cudaFree(c->fft[i]);
+    }
     if (c->prof_ev) {
         for (int i = 0; i < 2 * c->prof_max; ++i) cudaEventDestroy(c->prof_ev[i]);
         free(c->prof_ev);
@@ -473,6 +485,13 @@ ENOMR_API enomr_status enomr_init(enomr_ctx **out, int eq, int ndim, int64_t nx,
               cudaMalloc(&c->ayb, sizeof(double) * 3 * nx) == cudaSuccess &&
               cudaMalloc(&c->Ub1, sizeof(double) * c->nstate) == cudaSuccess &&
               cudaMalloc(&c->Ub2, sizeof(double) * c->nstate) == cudaSuccess;
+    if (ok && eq == ENOMR_EULER) {
+        c->nsel = ndim == 2 ? 8 * ny * (nx + 1) + 8 * nx * (ny + 1) : 6 * (nx + 1);
+        c->nft = ndim == 2 ? 4 * ny * (nx + 1) + 4 * nx * (ny + 1) : 3 * (nx + 1);
+        for (int i = 0; i < 2 && ok; ++i)
+            ok = cudaMalloc(&c->fsel[i], c->nsel) == cudaSuccess &&
+                 cudaMalloc(&c->fft[i], sizeof(double) * c->nft) == cudaSuccess;
+    }
     if (!ok) {
         cudaGetLastError();
         enomr_free(c);
@@ -509,7 +528,8 @@ static const double RK_C0[3] = {0.0, 0.75, 1.0 / 3.0};
 static const double RK_C1[3] = {1.0, 0.25, 2.0 / 3.0};
 
 static enomr_status stage_impl(enomr_ctx *c, int s, const double *Un, const double *Us,
-                               double *Uout, bool alpha_current = false)
+                               double *Uout, bool alpha_current = false, uint8_t *sel = nullptr,
+                               double *ft = nullptr)
 {
     enomr_status st = alpha_current ? ENOMR_OK : compute_alpha(c, Us, false);
     if (st) return st;
@@ -521,7 +541,7 @@ static enomr_status stage_impl(enomr_ctx *c, int s, const double *Un, const doub
     e.dt_dev = c->dt;
     e.Un = Un;
     e.out = Uout;
-    return rhs_with_epilogue(c, Us, e, nullptr);
+    return rhs_with_epilogue(c, Us, e, sel, ft);
 }
 
 ENOMR_API enomr_status enomr_stage(enomr_ctx *c, int s, const double *Un, const double *Us,
@@ -663,7 +683,8 @@ ENOMR_API enomr_status enomr_get_status(enomr_ctx *c)
 }
 
 static enomr_status rhs_vjp_impl(enomr_ctx *c, const double *U, const double *Lbar, double *Ubar,
-                                 double scale)
+                                 double scale, const uint8_t *sel_in = nullptr,
+                                 const double *ft_in = nullptr)
 {
     if (c->eq == ENOMR_ADVECTION) {
         AdvArgs a;
@@ -713,11 +734,15 @@ static enomr_status rhs_vjp_impl(enomr_ctx *c, const double *U, const double *Lb
     v.inv_h = 1.0 / c->dx;
     v.alpha = c->ax;
     v.alpha_bar = c->axb;
+    v.sel_in = sel_in;
+    v.ft_in = ft_in;
     CU_TRY(by_order<VjpF>(c->order, v, C, 0, c->stream));
     if (C == 4) {
         v.inv_h = 1.0 / c->dy;
         v.alpha = c->ay;
         v.alpha_bar = c->ayb;
+        v.sel_in = sel_in ? sel_in + 8LL * c->ny * (c->nx + 1) : nullptr;
+        v.ft_in = ft_in ? ft_in + 4LL * c->ny * (c->nx + 1) : nullptr;
         CU_TRY(by_order<VjpF>(c->order, v, C, 1, c->stream));
     }
     const long long nl = (C == 4) ? c->ny + c->nx : c->ny;
@@ -754,8 +779,15 @@ ENOMR_API enomr_status enomr_step_vjp(enomr_ctx *c, const double *Un, double dt,
     enomr_status st;
     // recompute the stages from the step's checkpoint U^n
     CU_TRY(launch_set_dt(c->smax, 0.0, dt, c->dt, c->stream));
-    if ((st = stage_impl(c, 1, Un, Un, c->U1))) return st;
-    if ((st = stage_impl(c, 2, Un, c->U1, c->U2))) return st;
+    // the recomputed stages also keep their selections and per-field values,
+    // which the transposes at U^n and U^(1) then reuse
+    const bool keep = c->eq == ENOMR_EULER;
+    if ((st = stage_impl(c, 1, Un, Un, c->U1, false, keep ? c->fsel[0] : nullptr,
+                         keep ? c->fft[0] : nullptr)))
+        return st;
+    if ((st = stage_impl(c, 2, Un, c->U1, c->U2, false, keep ? c->fsel[1] : nullptr,
+                         keep ? c->fft[1] : nullptr)))
+        return st;
     // U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2))
     if ((st = axpy(c, 1.0 / 3.0, Ubar_np1, Ubar_n, 0))) return st;
     if ((st = axpy(c, 2.0 / 3.0, Ubar_np1, c->Ub2, 0))) return st;
@@ -763,10 +795,13 @@ ENOMR_API enomr_status enomr_step_vjp(enomr_ctx *c, const double *Un, double dt,
     // U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
     if ((st = axpy(c, 0.75, c->Ub2, Ubar_n, 1))) return st;
     if ((st = axpy(c, 0.25, c->Ub2, c->Ub1, 0))) return st;
-    if ((st = rhs_vjp_impl(c, c->U1, c->Ub2, c->Ub1, 0.25 * dt))) return st;
+    if ((st = rhs_vjp_impl(c, c->U1, c->Ub2, c->Ub1, 0.25 * dt, keep ? c->fsel[1] : nullptr,
+                           keep ? c->fft[1] : nullptr)))
+        return st;
     // U1 = U^n + dt L(U^n)
     if ((st = axpy(c, 1.0, c->Ub1, Ubar_n, 1))) return st;
-    return rhs_vjp_impl(c, Un, c->Ub1, Ubar_n, dt);
+    return rhs_vjp_impl(c, Un, c->Ub1, Ubar_n, dt, keep ? c->fsel[0] : nullptr,
+                        keep ? c->fft[0] : nullptr);
 }
 
 ENOMR_API enomr_status enomr_debug_alpha(enomr_ctx *c, double *alpha_x, double *alpha_y,

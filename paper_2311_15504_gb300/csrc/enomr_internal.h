@@ -35,6 +35,7 @@ struct SweepArgs {
     const double *alpha;   // [lines][3]: max|un-c|, max|un|, max|un+c|
     double *alpha_next;    // 1D only: accumulate the output state's alpha here, or nullptr
     uint8_t *sel;          // optional selection dump for this sweep
+    double *ft_out;        // optional: f^+ + f^- per field and interface, [C][lines][nlen+1]
     int *status;
     Epilogue epi;
 };
@@ -114,6 +115,11 @@ struct VjpArgs {
     const double *alpha;  // [lines][3]
     double *alpha_bar;    // [lines][3], accumulated
     int *status;
+    // optional frozen forward data of this state (written by a forward
+    // sweep with sel / ft_out): when given, the kernel reads the selections
+    // and the per-field reconstructed values instead of recomputing them
+    const uint8_t *sel_in;
+    const double *ft_in;
 };
 
 template <int R> cudaError_t launch_sweep_vjp(const VjpArgs &a, int C, int dir, cudaStream_t s);

@@ -391,6 +391,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
                 A.sel[((0 * C + f) * nlines + Lg) * NI + k] = (uint8_t)(T + 2);
                 A.sel[((1 * C + f) * nlines + Lg) * NI + k] = (uint8_t)(T + 2);
             }
+            if (A.ft_out && valid) A.ft_out[(f * nlines + Lg) * (nlen + 1) + k] = fp + fm;
         }
     } else {
 #pragma unroll 1
@@ -414,6 +415,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
                 A.sel[((0 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selp;
                 A.sel[((1 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selm;
             }
+            if (A.ft_out && valid) A.ft_out[(f * nlines + Lg) * (nlen + 1) + k] = fp + fm;
         }
     }
     double Fh[C];
@@ -511,6 +513,7 @@ __global__ void __launch_bounds__(TP) k_batch_stage(BatchArgs B)
         A.alpha = B.alpha + 3 * pr;
         A.alpha_next = B.alpha_next ? B.alpha_next + 3 * pr : nullptr;
         A.sel = nullptr;
+        A.ft_out = nullptr;
         A.status = B.status;
         A.epi.mode = EPI_STAGE;
         A.epi.c0 = B.c0;

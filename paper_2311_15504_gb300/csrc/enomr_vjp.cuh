@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(TP *NL) k_sweep_vjp(VjpArgs A)
     __shared__ double sWB[NL][TP][2 * g];
     __shared__ double sQB[NL][TP][2 * g];
     __shared__ double sRow[NL][TP][3];
+    __shared__ double sRowA[NL][TP][4];
     __shared__ double sRoeB[NL][TP][2][C];
     __shared__ double sA[T * W];
 
@@ -203,18 +204,27 @@ __global__ void __launch_bounds__(TP *NL) k_sweep_vjp(VjpArgs A)
             q = fma(l1c, sF[1][line][s], q);
             return fma(l0c, sF[0][line][s], q);
         };
-        // forward: windows, frozen selection, value
-        double vp[W], vm[W];
-#pragma unroll
-        for (int j = 0; j < 2 * g; ++j) {
-            const double w = project_w(p + j), q = project_q(p + j);
-            if (j <= 2 * g - 2) vp[j] = fma(alpha, w, q);
-            if (j >= 1) vm[2 * g - 1 - j] = fma(-alpha, w, q);
-        }
+        // forward: frozen selection and value (given, or recomputed)
         int selp, selm;
-        const double fp = mr_value<R>(vp, sA, valid, selp);
-        const double fm = mr_value<R>(vm, sA, valid, selm);
-        ftv[f] = fp + fm;
+        if (A.sel_in) {
+            const long long NI = nlen + 1;
+            const long long kc = k <= nlen ? k : nlen;
+            const long long lc = Lg < nlines ? Lg : nlines - 1;
+            selp = A.sel_in[((0 * C + f) * nlines + lc) * NI + kc];
+            selm = A.sel_in[((1 * C + f) * nlines + lc) * NI + kc];
+            ftv[f] = A.ft_in[(f * nlines + lc) * NI + kc];
+        } else {
+            double vp[W], vm[W];
+#pragma unroll
+            for (int j = 0; j < 2 * g; ++j) {
+                const double w = project_w(p + j), q = project_q(p + j);
+                if (j <= 2 * g - 2) vp[j] = fma(alpha, w, q);
+                if (j >= 1) vm[2 * g - 1 - j] = fma(-alpha, w, q);
+            }
+            const double fp = mr_value<R>(vp, sA, valid, selp);
+            const double fm = mr_value<R>(vm, sA, valid, selm);
+            ftv[f] = fp + fm;
+        }
         // cotangent of this field's f^+ + f^-
         double ftb;
         if (f == 0) ftb = 0.25 * b1 * ph0_b;
@@ -235,27 +245,49 @@ __global__ void __launch_bounds__(TP *NL) k_sweep_vjp(VjpArgs A)
         if (selm == T) { wm[c0] = 0.5 * ftb; wm[c0 + 1] = 0.5 * ftb; }
         if (selm == T + 1) { wm[c0] = 1.5 * ftb; wm[c0 - 1] = -0.5 * ftb; }
         if (selm == T + 2) wm[c0] = ftb;
-        // reverse of split and projection, per window cell
-        double l0b = 0.0, l1b = 0.0, ltb = 0.0;
+        // reverse of split and projection, per window cell.  With d = P - M
+        // the cotangents are w_bar = alpha d and q_bar = P + M; the sums
+        // S[q] = sum_j d_j U_j[q] give both the U part of the row-coefficient
+        // cotangents (alpha S) and the alpha cotangent sum_j d_j w_j = l . S.
+        double S0 = 0.0, S1 = 0.0, ST = 0.0, SE = 0.0, Q0 = 0.0, Q1 = 0.0, QT = 0.0;
 #pragma unroll
         for (int j = 0; j < 2 * g; ++j) {
             const int s = p + j;
             const double P = (j <= 2 * g - 2) ? wp[j] : 0.0;
             const double M = (j >= 1) ? wm[2 * g - 1 - j] : 0.0;
-            const double w = project_w(s);
-            const double qb = P + M, d = P - M, wb = alpha * d;
-            ab[aidx] += w * d;
-            sWB[line][p][j] = wb;
+            const double qb = P + M, d = P - M;
+            sWB[line][p][j] = d;  // alpha is folded into the gather's row
             sQB[line][p][j] = qb;
-            l0b += wb * sU[0][line][s] + qb * sF[0][line][s];
+            S0 = fma(d, sU[0][line][s], S0);
+            Q0 = fma(qb, sF[0][line][s], Q0);
+            if (C == 4) ST = fma(d, sU[2][line][s], ST);
             if (!shear) {
-                l1b += wb * sU[1][line][s] + qb * sF[1][line][s];
-                if (C == 4) ltb += wb * sU[2][line][s] + qb * sF[2][line][s];
+                S1 = fma(d, sU[1][line][s], S1);
+                SE = fma(d, sU[C - 1][line][s], SE);
+                Q1 = fma(qb, sF[1][line][s], Q1);
+                if (C == 4) QT = fma(qb, sF[2][line][s], QT);
             }
         }
+        double l0b, l1b = 0.0, ltb = 0.0;
+        l0b = fma(alpha, S0, Q0);
+        if (shear) {
+            ab[aidx] += fma(l0c, S0, ST);
+        } else {
+            l1b = fma(alpha, S1, Q1);
+            if (C == 4) ltb = fma(alpha, ST, QT);
+            double a = fma(l0c, S0, SE);
+            a = fma(l1c, S1, a);
+            if (C == 4) a = fma(-vh, ST, a);
+            ab[aidx] += a;
+        }
+        // gather rows: U part scaled by alpha (it multiplies d), F part not
         sRow[line][p][0] = l0c;
         sRow[line][p][1] = l1c;
         sRow[line][p][2] = (C == 4) ? -vh : 0.0;
+        sRowA[line][p][0] = alpha * l0c;
+        sRowA[line][p][1] = alpha * l1c;
+        sRowA[line][p][2] = (C == 4) ? -alpha * vh : 0.0;
+        sRowA[line][p][3] = alpha;
         // row coefficients -> Roe scalars
         if (shear) {
             vh_b -= l0b;
@@ -292,23 +324,25 @@ __global__ void __launch_bounds__(TP *NL) k_sweep_vjp(VjpArgs A)
                 for (int j = 0; j < 2 * g; ++j) {
                     const int pp = s - j;
                     if (pp < 0 || pp >= TP) continue;
-                    const double wb = sWB[gl][pp][j], qb = sQB[gl][pp][j];
-                    const double r0 = sRow[gl][pp][0];
+                    const double d = sWB[gl][pp][j], qb = sQB[gl][pp][j];
+                    const double r0 = sRow[gl][pp][0], a0 = sRowA[gl][pp][0];
+                    const double al_ = sRowA[gl][pp][3];
                     if (shear) {
-                        cUb[c][0] += wb * r0;
-                        cUb[c][2] += wb;
+                        cUb[c][0] += d * a0;
+                        cUb[c][2] += d * al_;
                         cFb[c][0] += qb * r0;
                         cFb[c][2] += qb;
                     } else {
                         const double r1 = sRow[gl][pp][1], rt = sRow[gl][pp][2];
-                        cUb[c][0] += wb * r0;
-                        cUb[c][1] += wb * r1;
-                        cUb[c][C - 1] += wb;
+                        const double a1 = sRowA[gl][pp][1], at = sRowA[gl][pp][2];
+                        cUb[c][0] += d * a0;
+                        cUb[c][1] += d * a1;
+                        cUb[c][C - 1] += d * al_;
                         cFb[c][0] += qb * r0;
                         cFb[c][1] += qb * r1;
                         cFb[c][C - 1] += qb;
                         if (C == 4) {
-                            cUb[c][2] += wb * rt;
+                            cUb[c][2] += d * at;
                             cFb[c][2] += qb * rt;
                         }
                     }
