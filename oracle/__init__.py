@@ -28,7 +28,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-EQ_ADVECTION, EQ_EULER1D, EQ_EULER2D = 0, 1, 2
+EQ_ADVECTION, EQ_EULER1D, EQ_EULER2D, EQ_BURGERS = 0, 1, 2, 3
 BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
 ORC_OK, ORC_EINVAL, ORC_ENONPHYS = 0, 1, 4
 
@@ -70,6 +70,7 @@ def _load():
                 "orc_mr": (D, [I, P, I, P]),
                 "orc_mr_indicators": (I, [I, P, P, P, P, P]),
                 "orc_rhs_advection": (I, [L, P, D, I, I, D, P, P, P, P, P]),
+                "orc_rhs_burgers": (I, [L, P, D, I, I, P, P, P, P, P]),
                 "orc_rhs_euler1d": (I, [L, P, D, I, I, D, P, P, P, P, P, P]),
                 "orc_rhs_euler2d": (I, [L, L, P, D, D, I, I, D, P, P, P, P, P, P, P]),
                 "orc_euler_eigen": (I, [I, D, P, P, P, P, P]),
@@ -181,6 +182,31 @@ def rhs_advection(u, h, R, bc=BC_PERIODIC, a=1.0, forced=None, want_sel=False,
     cnt = ctypes.c_long(0)
     _check(_load().orc_rhs_advection(N, _p(u), h, R, bc, a, _p(fz), _p(sel), _p(win),
                                      _p(rhs), ctypes.byref(cnt)))
+    out = {"rhs": rhs}
+    if want_sel:
+        out["sel"] = sel.reshape(2, N + 1)
+    if want_win:
+        out["win"] = win.reshape(2, N + 1, 2 * g - 1)
+    if want_count:
+        out["ntested"] = cnt.value
+    return out
+
+
+def rhs_burgers(u, h, R, bc=BC_PERIODIC, forced=None, want_sel=False, want_win=False,
+                want_count=False):
+    """Inviscid Burgers (Sec. 4.2): f = u^2/2, unsplit where u keeps one sign
+    over the line, else the global Lax-Friedrichs split with alpha = max|u|.
+    Layouts as rhs_advection."""
+    u = _f64(u)
+    N = u.shape[0]
+    g = (R + 1) // 2
+    rhs = np.zeros(N)
+    sel = np.zeros(2 * (N + 1), dtype=np.uint8) if want_sel else None
+    win = np.zeros(2 * (N + 1) * (2 * g - 1)) if want_win else None
+    fz = None if forced is None else np.ascontiguousarray(forced, dtype=np.uint8)
+    cnt = ctypes.c_long(0)
+    _check(_load().orc_rhs_burgers(N, _p(u), h, R, bc, _p(fz), _p(sel), _p(win), _p(rhs),
+                                   ctypes.byref(cnt)))
     out = {"rhs": rhs}
     if want_sel:
         out["sel"] = sel.reshape(2, N + 1)
@@ -306,7 +332,8 @@ def euler_eigen(UL, UR, gamma=1.4):
 # Time integration
 # --------------------------------------------------------------------------
 class Problem:
-    """eq in {EQ_ADVECTION, EQ_EULER1D, EQ_EULER2D}; U layouts: (N,), (3,N), (4,ny,nx)."""
+    """eq in {EQ_ADVECTION, EQ_EULER1D, EQ_EULER2D, EQ_BURGERS}; U layouts: (N,),
+    (3,N), (4,ny,nx), (N,)."""
 
     def __init__(self, eq, R, nx, ny=1, dx=1.0, dy=1.0, bc=BC_PERIODIC, gamma=1.4, a=1.0):
         self.eq, self.R, self.nx, self.ny = eq, R, nx, ny

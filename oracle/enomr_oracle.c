@@ -325,29 +325,17 @@ static long ghost_index(long i, long N, int bc)
 /* sel layout: [side][interface], side 0 = f^+, 1 = f^-.                     */
 /* win layout: [side][interface][2g-1].                                      */
 /* ------------------------------------------------------------------------- */
-int orc_rhs_advection(long N, const double *u, double h, int R, int bc, double a,
-                      const uint8_t *forced, uint8_t *sel_out, double *win_out, double *rhs,
-                      long *ntested_out)
+/* Shared by the scalar equations: MR values of the split fluxes fp, fm
+ * (given on cells -g..N+g-1, index j+g), fhat = f^+ + f^- per interface and
+ * the flux difference of Eq. (1DWENOFD). */
+static void scalar_mr_rhs(const order_t *o, long N, const double *fp, const double *fm, double h,
+                          const uint8_t *forced, uint8_t *sel_out, double *win_out, double *rhs,
+                          long *ntested_out)
 {
-    const order_t *o = get_order(R);
+    const int g = o->g;
     long k, j;
-    int g;
-    double alpha;
-    double *fp, *fm, *fhat;
     long ntested = 0;
-    if (!o || N < 1 || !(h > 0)) return ORC_EINVAL;
-    g = o->g;
-    if (bc == 0 && N < 2 * g) return ORC_EINVAL;
-    alpha = dabs(a);
-    fp = (double *)malloc(sizeof(double) * (N + 2 * g));
-    fm = (double *)malloc(sizeof(double) * (N + 2 * g));
-    fhat = (double *)malloc(sizeof(double) * (N + 1));
-    for (j = -g; j < N + g; ++j) {
-        double uj = u[ghost_index(j, N, bc)];
-        double f = a * uj;
-        fp[j + g] = 0.5 * (f + alpha * uj);
-        fm[j + g] = 0.5 * (f - alpha * uj);
-    }
+    double *fhat = (double *)malloc(sizeof(double) * (N + 1));
 #pragma omp parallel for schedule(static) reduction(+ : ntested)
     for (k = 0; k <= N; ++k) {
         long i = k - 1; /* interface i+1/2 */
@@ -379,9 +367,83 @@ int orc_rhs_advection(long N, const double *u, double h, int R, int bc, double a
     }
     for (j = 0; j < N; ++j) rhs[j] = -(fhat[j + 1] - fhat[j]) / h;
     if (ntested_out) *ntested_out = ntested;
+    free(fhat);
+}
+
+int orc_rhs_advection(long N, const double *u, double h, int R, int bc, double a,
+                      const uint8_t *forced, uint8_t *sel_out, double *win_out, double *rhs,
+                      long *ntested_out)
+{
+    const order_t *o = get_order(R);
+    long j;
+    int g;
+    double alpha;
+    double *fp, *fm;
+    if (!o || N < 1 || !(h > 0)) return ORC_EINVAL;
+    g = o->g;
+    if (bc == 0 && N < 2 * g) return ORC_EINVAL;
+    alpha = dabs(a);
+    fp = (double *)malloc(sizeof(double) * (N + 2 * g));
+    fm = (double *)malloc(sizeof(double) * (N + 2 * g));
+    for (j = -g; j < N + g; ++j) {
+        double uj = u[ghost_index(j, N, bc)];
+        double f = a * uj;
+        fp[j + g] = 0.5 * (f + alpha * uj);
+        fm[j + g] = 0.5 * (f - alpha * uj);
+    }
+    scalar_mr_rhs(o, N, fp, fm, h, forced, sel_out, win_out, rhs, ntested_out);
     free(fp);
     free(fm);
-    free(fhat);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Inviscid Burgers equation u_t + (u^2/2)_x = 0 (Sec. 4.2).                  */
+/* f'(u) = u.  Where f' keeps one sign over the line (all u >= 0, or all      */
+/* u <= 0) the flux needs no splitting (the paper's remark for its test):    */
+/* f^+ = f, f^- = 0 (or f^+ = 0, f^- = f).  Otherwise the global             */
+/* Lax-Friedrichs split of Eq. (LF_Flux_Split) with alpha = max |u|.          */
+/* Layouts as orc_rhs_advection.                                             */
+/* ------------------------------------------------------------------------- */
+int orc_rhs_burgers(long N, const double *u, double h, int R, int bc, const uint8_t *forced,
+                    uint8_t *sel_out, double *win_out, double *rhs, long *ntested_out)
+{
+    const order_t *o = get_order(R);
+    long j;
+    int g, mode;
+    double umin, umax, alpha = 0.0;
+    double *fp, *fm;
+    if (!o || N < 1 || !(h > 0)) return ORC_EINVAL;
+    g = o->g;
+    if (bc == 0 && N < 2 * g) return ORC_EINVAL;
+    umin = u[0];
+    umax = u[0];
+    for (j = 0; j < N; ++j) {
+        if (!(u[j] == u[j])) return ORC_ENONPHYS;
+        umin = u[j] < umin ? u[j] : umin;
+        umax = u[j] > umax ? u[j] : umax;
+        alpha = dmax(alpha, dabs(u[j]));
+    }
+    mode = (umin >= 0.0) ? 0 : ((umax <= 0.0) ? 1 : 2);
+    fp = (double *)malloc(sizeof(double) * (N + 2 * g));
+    fm = (double *)malloc(sizeof(double) * (N + 2 * g));
+    for (j = -g; j < N + g; ++j) {
+        double uj = u[ghost_index(j, N, bc)];
+        double f = 0.5 * (uj * uj);
+        if (mode == 0) {
+            fp[j + g] = f;
+            fm[j + g] = 0.0;
+        } else if (mode == 1) {
+            fp[j + g] = 0.0;
+            fm[j + g] = f;
+        } else {
+            fp[j + g] = 0.5 * (f + alpha * uj);
+            fm[j + g] = 0.5 * (f - alpha * uj);
+        }
+    }
+    scalar_mr_rhs(o, N, fp, fm, h, forced, sel_out, win_out, rhs, ntested_out);
+    free(fp);
+    free(fm);
     return ORC_OK;
 }
 
@@ -870,7 +932,7 @@ int orc_rhs_euler2d_alpha(long nx, long ny, const double *U, double dx, double d
 
 /* ------------------------------------------------------------------------- */
 /* Generic RHS dispatcher used by the time integrators.                      */
-/* eq: 0 advection (uses a), 1 Euler 1D, 2 Euler 2D.                          */
+/* eq: 0 advection (uses a), 1 Euler 1D, 2 Euler 2D, 3 Burgers.              */
 /* ------------------------------------------------------------------------- */
 typedef struct {
     int eq, R, bc;
@@ -880,7 +942,7 @@ typedef struct {
 
 static long prob_size(const problem_t *P)
 {
-    if (P->eq == 0) return P->nx;
+    if (P->eq == 0 || P->eq == 3) return P->nx;
     if (P->eq == 1) return 3 * P->nx;
     return 4 * P->nx * P->ny;
 }
@@ -889,6 +951,8 @@ static int prob_rhs(const problem_t *P, const double *U, double *rhs)
 {
     if (P->eq == 0)
         return orc_rhs_advection(P->nx, U, P->dx, P->R, P->bc, P->a, NULL, NULL, NULL, rhs, NULL);
+    if (P->eq == 3)
+        return orc_rhs_burgers(P->nx, U, P->dx, P->R, P->bc, NULL, NULL, NULL, rhs, NULL);
     if (P->eq == 1)
         return orc_rhs_euler1d(P->nx, U, P->dx, P->R, P->bc, P->gamma, NULL, NULL, NULL, rhs, NULL,
                                NULL);
@@ -904,8 +968,8 @@ int orc_rhs(int eq, long nx, long ny, double dx, double dy, int R, int bc, doubl
     return prob_rhs(&P, U, rhs);
 }
 
-/* CFL time step (reading C-13): 1D dt = cfl*h / max(|u|+c) (advection:
- * cfl*h/|a|); 2D dt = cfl / max((|u|+c)/dx + (|v|+c)/dy). */
+/* CFL time step: 1D dt = cfl*h / max(|u|+c) (advection: cfl*h/|a|;
+ * Burgers: cfl*h/max|u|); 2D dt = cfl / max((|u|+c)/dx + (|v|+c)/dy). */
 int orc_cfl_dt(int eq, long nx, long ny, double dx, double dy, double gamma, double a,
                const double *U, double cfl, double *dt)
 {
@@ -914,6 +978,12 @@ int orc_cfl_dt(int eq, long nx, long ny, double dx, double dy, double gamma, dou
     if (eq == 0) {
         if (!(dabs(a) > 0)) return ORC_EINVAL;
         *dt = cfl * dx / dabs(a);
+        return ORC_OK;
+    }
+    if (eq == 3) {
+        for (i = 0; i < nx; ++i) smax = dmax(smax, dabs(U[i]));
+        if (!(smax > 0)) return ORC_EINVAL;
+        *dt = cfl * dx / smax;
         return ORC_OK;
     }
     for (i = 0; i < n; ++i) {

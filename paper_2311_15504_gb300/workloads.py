@@ -58,6 +58,22 @@ def advection_step(n: int):
 
 
 # ---------------------------------------------------------------------------
+# Inviscid Burgers (Sec. 4.2)
+# ---------------------------------------------------------------------------
+def burgers_sine3(n: int, lam: float = 1.0):
+    """u0 = lam (1 + 0.5 sin^3(pi x)) on [0, 2], periodic; n unknowns."""
+    x, h = periodic_grid(0.0, 2.0, n)
+    return lam * (1.0 + 0.5 * np.sin(np.pi * x) ** 3), h
+
+
+def burgers_dt(order: int, h: float, lam: float = 1.0):
+    """Time step of the Burgers accuracy test (Sec. 4.2): proportional to
+    h^(R/3)/lam so that the SSP-RK3 error matches the order in space."""
+    c = {5: 1.0, 9: 1e2, 13: 1e4, 17: 1e6}[order]
+    return c * h ** (order / 3.0) / lam
+
+
+# ---------------------------------------------------------------------------
 # 1D Euler
 # ---------------------------------------------------------------------------
 def shock_entropy(n: int, gamma=GAMMA):
