@@ -4,7 +4,8 @@
 Workload: 2D Euler (gamma = 1.4) four-quadrant Riemann problem on [0,1]^2,
 interface at (0.8, 0.8), quadrant states drawn with seed = rank, 4096^2 cells,
 ENO-MR order 9, transmissive boundaries, SSP-RK3 with the CFL 0.5 step
-computed on the device.  One benchmark step = one SSP-RK3 step (3 stages).
+computed on the device.  One benchmark step = one SSP-RK3 step (3 stages);
+the default 100 steps from t = 0 are the workload's whole run.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
 host cores instead (test infrastructure, not the product path).
@@ -32,7 +33,7 @@ UNIT = "cell-updates/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096)
@@ -40,7 +41,7 @@ def parse():
     ap.add_argument("--cfl", type=float, default=0.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--only", choices=["adjoint", "batched"], default=None,
+    ap.add_argument("--only", choices=["adjoint", "batched", "vortex"], default=None,
                     help="run one secondary measurement alone (profiling aid)")
     return ap.parse_args()
 
@@ -49,6 +50,7 @@ def config(a):
     return {"workload": "euler2d_quadrant_riemann", "grid": [a.n, a.n], "order": a.order,
             "cfl": a.cfl, "bc": "transmissive", "time_integrator": "SSP-RK3",
             "step": "one SSP-RK3 step = 3 RK stages", "seed": "rank",
+            "run": f"{a.steps} SSP-RK3 steps from t = 0",
             "l2": "inputs larger than L2 (one state is %.0f MB)" % (4 * 8 * a.n * a.n / 1e6)}
 
 
@@ -111,46 +113,74 @@ class ClockSampler:
 # algorithmic FP64 work of one sweep launch (counted per interface; an FMA is
 # two flops, an add, multiply, divide or square root one)
 # ---------------------------------------------------------------------------
-def sweep_flops(order, C, sel, n_interfaces, n_flat=0, stage_epilogue=False):
-    """Flops of one Euler sweep.  Every interface (one per cell): the cell's
-    primitives and normal flux (18), the flux difference (2C), the stage
-    update when the sweep carries it (4C: add of the other sweep, axpy and
-    combination), the Roe average and scaled eigenvectors (28) and the
-    back-projection (C == 4: 20, C == 3: 14).
-    Interfaces whose two sides have flat windows (three equal cell states at
-    the side's centre: IS_0 = 0 exactly, minmod returns v(0)) add only the
-    projection of their two centre cells (40 flops per cell for C = 4, 24 for
-    C = 3: 20 or 12 FMAs for U and F) and one split FMA per field and side.
-    Other interfaces add the projection of the 2g-cell window, the split
-    (2 FMAs per window value and side) and, per window, the baseline
-    indicator (8), the indicators of the tested candidates up to the chosen
-    one (2|S|-1 each; none when IS_0 = 0), the reconstruction on the chosen
-    stencil (2|S|-1) or the minmod fma (2).  sel: selection histogram
-    counts[T+3] over all windows of the launch (flat interfaces included)."""
+def sweep_work(order, C, sel, n_interfaces, counts, stage_epilogue=False):
+    """Algorithmic work of one Euler sweep as (flops, FP64 operations).
+
+    Operations are FP64-pipe operations of a minimal evaluation: fma, mul,
+    add, div and rsqrt count 1 each (div and rsqrt as one operation, though
+    the hardware evaluates them with several); flops count an fma as 2.
+    Sign flips, |x|, min/max and compares, which the kernels do on the
+    integer ALU, count 0.  (ops, flops) per part, C = 4 / C = 3:
+
+    every interface (one per cell of the line):
+      the cell's primitives and normal flux        15, 18 / 12, 14
+      Roe eigen-quantities and scaled rows of L    16, 19 / 15, 17
+      back-projection F = R (f^+ + f^-)            19, 24 / 16, 19
+      flux difference of the cell                  2C, 2C
+      stage update when the sweep carries it       4C, 6C (add of the other
+                                                   sweep, 2 fma, 1 mul)
+    the Roe average, where the centre states differ 11, 14 / 8, 10
+    flat interfaces (both sides: three equal cell states at the side's
+    centre, so IS_0 = 0 exactly and minmod returns v(0)):
+      projection of the centre cells               20, 40 / 12, 24 each
+                                                   (one projection when the
+                                                   two centre states are equal)
+      per field: two split fmas and f^+ + f^-      3, 5
+    other interfaces:
+      projection of the 2g-cell window             20, 40 / 12, 24 per cell
+      per field: split of 2(2g-1) values and f^+ + f^-
+      per window (2C): the baseline indicator      6, 8
+        the indicators of the tested candidates up to the chosen one
+                                                   |S|, 2|S|-1 each
+        (none when IS_0 = 0), and the reconstruction on the chosen stencil
+        (|S|, 2|S|-1) or the minmod fma (1, 2).
+    sel: selection histogram counts[T+3] over all windows of the launch
+    (flat interfaces included); counts: (flat, flat with equal centre
+    states, equal centre states) interface counts."""
     import oracle  # table sizes only
+    n_flat, n_flat_eq, n_eq = counts
     g = (order + 1) // 2
     T = oracle.num_tested(order)
-    sizes = [oracle.candidate(order, t)[0] + oracle.candidate(order, t)[1] + 1 for t in range(T)]
-    cell = 40 if C == 4 else 24
-    fixed = 18 + 2 * C + (4 * C if stage_epilogue else 0) + 28 + (20 if C == 4 else 14)
-    full = fixed + cell * 2 * g + C * 2 * 2 * (2 * g - 1)
-    flat = fixed + cell * 2 + C * 2 * 2 + C
-    flops = float(n_flat) * flat + float(n_interfaces - n_flat) * full
-    walk_cum = np.cumsum([2 * s - 1 for s in sizes])
-    counts = np.asarray(sel, dtype=np.float64).copy()
-    counts[T + 2] -= 2 * C * n_flat  # the flat interfaces' windows
+    sizes = np.array([oracle.candidate(order, t)[0] + oracle.candidate(order, t)[1] + 1
+                      for t in range(T)], dtype=np.float64)
+    four = C == 4
+    proj = np.array([20, 40] if four else [12, 24], dtype=np.float64)
+    fixed = (np.array([15, 18] if four else [12, 14]) + np.array([16, 19] if four else [15, 17])
+             + np.array([19, 24] if four else [16, 19]) + 2 * C
+             + (np.array([4 * C, 6 * C]) if stage_epilogue else 0)).astype(np.float64)
+    roe_avg = np.array([11, 14] if four else [8, 10], dtype=np.float64)
+    w = float(n_interfaces) * fixed + float(n_interfaces - n_eq) * roe_avg
+    w += float(n_flat_eq) * proj + float(n_flat - n_flat_eq) * 2 * proj
+    w += float(n_flat) * C * np.array([3, 5])
+    split = np.array([2 * (2 * g - 1) + 1, 4 * (2 * g - 1) + 1], dtype=np.float64)
+    w += float(n_interfaces - n_flat) * (proj * 2 * g + C * split)
+    cum = np.stack([np.cumsum(sizes), np.cumsum(2 * sizes - 1)], axis=1)  # walk to t
+    cnt = np.asarray(sel, dtype=np.float64).copy()
+    cnt[T + 2] -= 2 * C * n_flat  # the flat interfaces' windows
+    base = np.array([6, 8], dtype=np.float64)
     for t in range(T):
-        flops += counts[t] * (8 + walk_cum[t] + 2 * sizes[t] - 1)
+        w += cnt[t] * (base + cum[t] + np.array([sizes[t], 2 * sizes[t] - 1]))
     # minmod outcomes: S(0,1) and S(1,0) come after a full walk; S(0,0) is
     # counted as the IS_0 = 0 shortcut (lower bound)
-    flops += (counts[T] + counts[T + 1]) * (8 + walk_cum[-1] + 2)
-    flops += counts[T + 2] * (8 + 2)
-    return float(flops)
+    w += (cnt[T] + cnt[T + 1]) * (base + cum[-1] + np.array([1, 2]))
+    w += cnt[T + 2] * (base + np.array([1, 2]))
+    return float(w[1]), float(w[0])
 
 
 def flat_interfaces(U, axis):
-    """Interfaces of a transmissive 2D sweep (axis 0: x, 1: y) whose plus and
-    minus windows are flat in the sense of the kernel's shortcut."""
+    """Interface counts of a transmissive 2D sweep (axis 0: x, 1: y):
+    (flat, flat with bitwise-equal centre states, bitwise-equal centre
+    states), flatness in the sense of the kernel's shortcut."""
     import torch
     X = U if axis == 0 else U.transpose(1, 2)
     Xp = torch.nn.functional.pad(X.unsqueeze(0), (3, 3, 0, 0), mode="replicate")[0]
@@ -158,7 +188,44 @@ def flat_interfaces(U, axis):
     nI = X.shape[2] + 1
     e = [eq[:, o:o + nI] for o in range(5)]            # e_o: cells k-3+o, k-2+o
     flat = ((e[0] & e[1]) | (e[2] & e[3])) & ((e[3] & e[4]) | (e[1] & e[2]))
-    return int(flat.sum().item())
+    return (int(flat.sum().item()), int((flat & e[2]).sum().item()), int(e[2].sum().item()))
+
+
+KERNEL_SOURCES = ("enomr_sweep.cuh", "enomr_kernels.cuh", "enomr_common.cuh", "gen_coeffs.py")
+
+
+def kernel_source_digest():
+    """sha256 over the sources that define the sweep kernels (code and tile
+    shapes)."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2311_15504_gb300", "csrc")
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kname, n, order):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary of this workload, or None when that summary was taken on other
+    kernel sources (or does not cover this kernel and size)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
+                        f"euler2d_riemann_{n}_r{order}_launches.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    rec = {}
+    for ln in lines:
+        if ln.startswith("    ") or ":" not in ln:
+            continue
+        k, _, v = ln.partition(":")
+        rec[k.strip().strip("`")] = v.strip().strip("`")
+    if rec.get("kernel sources sha256") != kernel_source_digest():
+        return None
+    v = rec.get(f"dram bytes per launch {kname}")
+    return float(v) if v else None
 
 
 def batched_gain(enomr, workloads, dev, a, nprob=4096, order=9, reps=5):
@@ -263,6 +330,68 @@ def adjoint_ratio(enomr, workloads, dev, n=1024, order=9, steps=10, cfl=0.5):
             "forward_includes_checkpoint_copy": True}
 
 
+def sweep_fracs(enomr, solver, U, order, n, cfl, peak_ops, steps=2):
+    """FP64-operation roofline fractions of the x and y sweeps of `steps`
+    SSP-RK3 steps from state U (each sweep timed live on the library's
+    stream; work from the selections and flat-interface counts of U)."""
+    import torch
+    T = enomr.num_tested(order)
+    nsx = 8 * n * (n + 1)
+    sel = solver.selection(U)
+    hx = torch.bincount(sel[:nsx].long(), minlength=T + 3).cpu().numpy()
+    hy = torch.bincount(sel[nsx:].long(), minlength=T + 3).cpu().numpy()
+    wx = sweep_work(order, 4, hx, n * (n + 1), flat_interfaces(U, 0))
+    wy = sweep_work(order, 4, hy, n * (n + 1), flat_interfaces(U, 1), stage_epilogue=True)
+    out = {}
+    for kind, w in ((1, wx), (2, wy)):
+        Uc = U.clone()
+        solver.profile_begin(kind, 3 * steps)
+        for _ in range(steps):
+            solver.step(Uc, 0.0, cfl)
+        nl, ms = solver.profile_end()
+        out["x" if kind == 1 else "y"] = round(w[1] / (ms / max(nl, 1) * 1e-3) / peak_ops, 4)
+    return out
+
+
+def aggregate_ranks(ms_local, cell_updates_per_rank, device):
+    """Whole-job rate of independent replicas: the max over ranks of the
+    timed region (ms) and all ranks' cell-updates divided by it."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max = float(t.item())
+    return ms_max, world * cell_updates_per_rank / (ms_max * 1e-3)
+
+
+def vortex_rate(enomr, workloads, dev, a):
+    """Smooth workload (no flat windows): isentropic vortex, periodic, CFL
+    steps; W warm-up steps, then K timed steps."""
+    import torch
+    Uv, hv, _ = workloads.isentropic_vortex(a.n)
+    sv = enomr.Solver(enomr.EULER, (a.n, a.n), order=a.order, dx=hv, dy=hv,
+                      bc=enomr.PERIODIC, device=dev)
+    U = torch.from_numpy(Uv).to(dev)
+    for _ in range(a.warmup):
+        sv.step(U, 0.0, a.cfl)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(a.steps):
+        sv.step(U, 0.0, a.cfl)
+    f1.record()
+    torch.cuda.synchronize()
+    sv.check_status()
+    sv.close()
+    return {"workload": f"isentropic vortex {a.n}^2 periodic, order {a.order}",
+            "value": a.n * a.n * 3 * a.steps / (f0.elapsed_time(f1) * 1e-3), "unit": UNIT,
+            "ms_per_step": f0.elapsed_time(f1) / a.steps}
+
+
 def main_ours(a):
     import torch
     import torch.distributed as dist
@@ -302,13 +431,8 @@ def main_ours(a):
     ms = e0.elapsed_time(e1)
     nx_launch, x_ms = s.profile_end()
     s.check_status()
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    ms_max = float(t.item())
     cells = n * n
-    value = world * cells * 3 * a.steps / (ms_max * 1e-3)
+    ms_max, value = aggregate_ranks(ms, cells * 3 * a.steps, dev)
     launches_per_step = 1 + 3 + 2 * 3  # dt, 3 alpha reductions, 2 sweeps x 3 stages
 
     extras = {}
@@ -319,43 +443,71 @@ def main_ours(a):
         for _ in range(a.steps):
             s.step(Uy, 0.0, a.cfl)
         ny_launch, y_ms = s.profile_end()
+        Uy.copy_(torch.from_numpy(U0))
         s.profile_begin(3, 3 * a.steps)
         for _ in range(a.steps):
             s.step(Uy, 0.0, a.cfl)
         na_launch, a_ms = s.profile_end()
-        # selection histogram of the final state: algorithmic work of a sweep
+        # algorithmic work of a sweep: selection histograms and flat-interface
+        # counts of the step states of the same trajectory (U^n of every
+        # sampled step stands in for its three stage states), averaged
         T = enomr.num_tested(R)
-        sel = s.selection(U)
         nsx = 8 * n * (n + 1)
-        hx = torch.bincount(sel[:nsx].long(), minlength=T + 3).cpu().numpy()
-        hy = torch.bincount(sel[nsx:].long(), minlength=T + 3).cpu().numpy()
-        fx_flat = flat_interfaces(U, 0)
-        fy_flat = flat_interfaces(U, 1)
-        fl_x = sweep_flops(R, 4, hx, n * (n + 1), fx_flat)
-        fl_y = sweep_flops(R, 4, hy, n * (n + 1), fy_flat, stage_epilogue=True)
-        extras["flat_interface_fraction"] = [fx_flat / (n * (n + 1)), fy_flat / (n * (n + 1))]
+        every = max(1, a.steps // 20)
+        Us = torch.from_numpy(U0).to(dev)
+        hx = np.zeros(T + 3)
+        hy = np.zeros(T + 3)
+        cx = np.zeros(3)
+        cy = np.zeros(3)
+        ns = 0
+        for it in range(a.steps):
+            if it % every == 0:
+                sel = s.selection(Us)
+                hx += torch.bincount(sel[:nsx].long(), minlength=T + 3).cpu().numpy()
+                hy += torch.bincount(sel[nsx:].long(), minlength=T + 3).cpu().numpy()
+                cx += np.array(flat_interfaces(Us, 0))
+                cy += np.array(flat_interfaces(Us, 1))
+                ns += 1
+            s.step(Us, 0.0, a.cfl)
+        hx, hy, cx, cy = hx / ns, hy / ns, cx / ns, cy / ns
+        del Us
+        wx = sweep_work(R, 4, hx, n * (n + 1), cx)
+        wy = sweep_work(R, 4, hy, n * (n + 1), cy, stage_epilogue=True)
+        extras["flat_interface_fraction"] = [cx[0] / (n * (n + 1)), cy[0] / (n * (n + 1))]
         probe, _ = enomr.probe_fp64_fma(iters=20000, device=dev)
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
-        # 2 DFMA lanes per SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
-        # peak_sustained = 2 / SM / cycle), 2 flops per DFMA, at the measured SM clock
-        peak = 2.0 * 2.0 * sms * mhz * 1e6 / 1e12
+        # 2 FP64 lanes per SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+        # peak_sustained = 2 / SM / cycle; DMUL and DADD take the same slots), at the
+        # median SM clock of the timed region
+        peak_ops = 2.0 * sms * mhz * 1e6
         x_avg = x_ms / max(nx_launch, 1)
         y_avg = y_ms / max(ny_launch, 1)
-        dom, avg, fl = ("x_sweep", x_avg, fl_x) if x_avg >= y_avg else ("y_sweep", y_avg, fl_y)
-        achieved = fl / (avg * 1e-3) / 1e12
+        if x_avg >= y_avg:
+            dom, avg, (fl, ops) = 0, x_avg, wx
+        else:
+            dom, avg, (fl, ops) = 1, y_avg, wy
+        kname = f"k_sweep<{R},4,{dom}>"
+        achieved = ops / (avg * 1e-3)
         extras["roofline"] = {
-            "bound": "alu", "pipe": "fp64", "kernel": f"k_sweep<{R},4,{0 if dom == 'x_sweep' else 1}>",
-            "achieved": round(achieved, 4), "peak": round(peak, 4),
-            "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-            "peak_source": (f"unit counts x clock: 2 DFMA/clk/SM x 2 flop x {sms} SMs x "
+            "bound": "alu", "pipe": "fp64", "kernel": kname,
+            "achieved": round(achieved / 1e9, 2), "peak": round(peak_ops / 1e9, 2),
+            "unit": "GFP64op/s", "frac": round(achieved / peak_ops, 4),
+            "peak_source": (f"unit counts x clock: 2 FP64 ops/clk/SM x {sms} SMs x "
                             f"{mhz:.0f} MHz (median SM clock of the timed region)"),
-            "peak_probe_tflops": round(probe / 1e12, 4),
-            "traffic": None,
-            "avg_launch_ms": round(avg, 4), "algorithmic_flops_per_launch": fl,
+            "op_definition": "fma, mul, add, div, rsqrt = 1 FP64 operation each",
+            "traffic": recorded_traffic(kname, n, R),
+            "avg_launch_ms": round(avg, 4), "algorithmic_ops_per_launch": ops,
+            "algorithmic_flops_per_launch": fl,
+            "achieved_tflops": round(fl / (avg * 1e-3) / 1e12, 4),
+            "frac_of_fma_flop_peak": round(fl / (avg * 1e-3) / (2.0 * peak_ops), 4),
+            "fp64_fma_probe_tflops": round(probe / 1e12, 4),
             "x_sweep_ms": round(x_avg, 4), "y_sweep_ms": round(y_avg, 4),
+            "x_sweep_frac": round(wx[1] / (x_avg * 1e-3) / peak_ops, 4),
+            "y_sweep_frac": round(wy[1] / (y_avg * 1e-3) / peak_ops, 4),
             "alpha_ms": round(a_ms / max(na_launch, 1), 4)}
-        extras["selection_histogram_x"] = hx.tolist()
+        extras["selection_histogram_x"] = [round(float(v)) for v in hx]
+        extras["work_samples"] = ns
         # every order on the same workload, a smooth workload, and the scalar
         # advection throughput case (each: 1 warm-up step, 2 timed steps)
         def rate(solver, Ustate, steps=2, dt=0.0):
@@ -368,19 +520,28 @@ def main_ours(a):
                 solver.step(Ustate, dt, a.cfl)
             f1.record()
             torch.cuda.synchronize()
-            return Ustate[0].numel() * 3 * steps / (f0.elapsed_time(f1) * 1e-3)
-        per_order = {}
+            cells = Ustate[0].numel() if Ustate.dim() > 1 else Ustate.numel()
+            return cells * 3 * steps / (f0.elapsed_time(f1) * 1e-3)
+        per_order, per_order_frac = {}, {}
         for Rk in enomr.ORDERS:
             sk = enomr.Solver(enomr.EULER, (n, n), order=Rk, dx=dx, dy=dy,
                               bc=enomr.TRANSMISSIVE, device=dev)
-            per_order[str(Rk)] = rate(sk, torch.from_numpy(U0).to(dev))
+            Uk = torch.from_numpy(U0).to(dev)
+            per_order[str(Rk)] = rate(sk, Uk)
+            per_order_frac[str(Rk)] = sweep_fracs(enomr, sk, Uk, Rk, n, a.cfl, peak_ops)
             sk.close()
-        extras["per_order_riemann"] = {"unit": UNIT, "values": per_order}
+        extras["per_order_riemann"] = {"unit": UNIT, "values": per_order,
+                                       "fp64_op_frac": per_order_frac,
+                                       "run": "1 warm-up + 2 timed steps from t = 0; "
+                                              "fractions over the next 2 steps"}
         Uv, hv, _ = workloads.isentropic_vortex(n)
         sv = enomr.Solver(enomr.EULER, (n, n), order=R, dx=hv, dy=hv, bc=enomr.PERIODIC,
                           device=dev)
+        Uvd = torch.from_numpy(Uv).to(dev)
         extras["smooth_vortex"] = {"workload": f"isentropic vortex {n}^2 periodic, order {R}",
-                                   "value": rate(sv, torch.from_numpy(Uv).to(dev)), "unit": UNIT}
+                                   "value": rate(sv, Uvd), "unit": UNIT,
+                                   "fp64_op_frac": sweep_fracs(enomr, sv, Uvd, R, n, a.cfl,
+                                                               peak_ops)}
         sv.close()
         adv = {}
         for Rk in (5, 9, 17):
@@ -401,6 +562,16 @@ def main_ours(a):
             sa.close()
         extras["advection_2p24"] = {"workload": "advection sin(pi x), N=2^24, periodic",
                                     "unit": UNIT, "values": adv}
+        burg = {}
+        for Rk in (5, 9, 17):
+            ub, hb = workloads.burgers_sine3(1 << 24)
+            sb = enomr.Solver(enomr.BURGERS, 1 << 24, order=Rk, dx=hb, bc=enomr.PERIODIC,
+                              device=dev)
+            burg[str(Rk)] = rate(sb, torch.from_numpy(ub).to(dev), steps=4)
+            sb.close()
+        extras["burgers_2p24"] = {"workload": "Burgers 1 + 0.5 sin^3(pi x) on [0,2], N=2^24, "
+                                              "periodic, CFL 0.5 steps",
+                                  "unit": UNIT, "values": burg}
         extras["batched"] = batched_gain(enomr, workloads, dev, a)
         extras["adjoint"] = adjoint_ratio(enomr, workloads, dev)
         # end to end through the public API with host buffers
@@ -466,10 +637,24 @@ def cpu_baseline(a, budget_s=20.0):
     t0 = time.perf_counter()
     P.step_ssprk3(U0, dt)
     el = time.perf_counter() - t0
-    return {"value": m * m * 3 / el, "unit": UNIT, "cores": oracle.num_threads(),
+    cores = oracle.num_threads()
+    # the same step on one host thread, on a grid a quarter of the size
+    # (results are bitwise the same for any thread count)
+    m1 = max(m // 4, 128)
+    P1, U1 = _oracle_problem(a, m1)
+    oracle.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        P1.step_ssprk3(U1, P1.cfl_dt(U1, a.cfl))
+        el1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(cores)
+    return {"value": m * m * 3 / el, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": f"one oracle SSP-RK3 step (3 stages) of the same workload on a "
-                      f"{m}x{m} grid ({el:.1f} s wall)"}
+                      f"{m}x{m} grid ({el:.1f} s wall)",
+            "single_thread": {"value": m1 * m1 * 3 / el1, "unit": UNIT, "cores": 1,
+                              "sample": f"one step on a {m1}x{m1} grid ({el1:.1f} s wall)"}}
 
 
 def main_reference(a):
@@ -513,6 +698,8 @@ def main_only(a):
     torch.cuda.set_device(dev)
     if a.only == "adjoint":
         out = adjoint_ratio(enomr, workloads, dev, n=a.n, steps=a.steps)
+    elif a.only == "vortex":
+        out = vortex_rate(enomr, workloads, dev, a)
     else:
         out = batched_gain(enomr, workloads, dev, a)
     print(json.dumps({"only": a.only, **out}), flush=True)

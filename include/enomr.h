@@ -55,15 +55,21 @@ typedef enum {
     ENOMR_ETIMEOUT = 5  /* reserved: a bounded device wait gave up          */
 } enomr_status;
 
-typedef enum { ENOMR_ADVECTION = 0, ENOMR_EULER = 1 } enomr_eq;
+typedef enum { ENOMR_ADVECTION = 0, ENOMR_EULER = 1, ENOMR_BURGERS = 2 } enomr_eq;
 typedef enum { ENOMR_PERIODIC = 0, ENOMR_TRANSMISSIVE = 1 } enomr_bc;
 
 typedef struct enomr_ctx enomr_ctx;
 
 /*
  * enomr_init -- create a solver context for one problem.
- *   eq         ENOMR_ADVECTION (f(u) = adv_speed * u, ndim must be 1) or
- *              ENOMR_EULER (ideal gas, gamma > 1; ndim 1 or 2).
+ *   eq         ENOMR_ADVECTION (f(u) = adv_speed * u, ndim must be 1),
+ *              ENOMR_EULER (ideal gas, gamma > 1; ndim 1 or 2) or
+ *              ENOMR_BURGERS (f(u) = u^2/2, Sec. 4.2; ndim must be 1).
+ *              Burgers: where u keeps one sign over the line (f' = u) the
+ *              flux is not split (f^+ = f, f^- = 0, or the mirror), as the
+ *              paper does for its test; otherwise the global Lax-Friedrichs
+ *              split with alpha = max |u| (Eq. LF_Flux_Split).  The CFL step
+ *              is cfl * dx / max |u| (0 for u = 0, a steady state).
  *   nx, ny     cells per direction (ny = 1 for ndim = 1).
  *   dx, dy     spacing h of Sec. 2.1 (dy ignored in 1D).
  *   order      R = 2r-1 in {5,7,9,11,13,15,17}: the (2r-1)-point ENO-MR scheme
@@ -167,6 +173,7 @@ ENOMR_API enomr_status enomr_get_status(enomr_ctx *ctx);
  *   choices L(U) makes.  U, Lbar, Ubar: device, state layout; Ubar must not
  *   alias U or Lbar.  Contributions of cells shared by neighbouring tiles
  *   are added with atomics, so the last bits may vary from run to run.
+ *   Advection and Euler only: ENOMR_EINVAL for a Burgers context.
  */
 ENOMR_API enomr_status enomr_rhs_vjp(enomr_ctx *ctx, const double *U, const double *Lbar,
                                      double *Ubar, double scale, int accumulate);
@@ -187,6 +194,7 @@ ENOMR_API enomr_status enomr_debug_alpha(enomr_ctx *ctx, double *alpha_x, double
  *   The stage states are recomputed from U_n (a per-step checkpoint) in the
  *   context's stage buffers; three enomr_rhs_vjp evaluations follow.
  *   U_n_bar is overwritten and must not alias U_n or U_np1_bar.
+ *   Advection and Euler only: ENOMR_EINVAL for a Burgers context.
  */
 ENOMR_API enomr_status enomr_step_vjp(enomr_ctx *ctx, const double *U_n, double dt,
                                       const double *U_np1_bar, double *U_n_bar);

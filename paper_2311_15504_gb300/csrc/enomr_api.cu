@@ -212,7 +212,48 @@ __global__ void k_axpy(long long n, double a, const double *x, double *y, int ac
 
 __global__ void k_set_dt(const double *smax, double cfl, double dt_fixed, double *dt)
 {
-    *dt = dt_fixed > 0.0 ? dt_fixed : cfl / *smax;
+    // a state without any wave speed (Burgers with u = 0) is steady: dt = 0
+    *dt = dt_fixed > 0.0 ? dt_fixed : (*smax > 0.0 ? cfl / *smax : 0.0);
+}
+
+// Burgers: max |u| over the line (the Lax-Friedrichs alpha and the CFL
+// speed, f'(u) = u) and which signs occur.  speed[0] and speed[1] are
+// zeroed before the launch; maxima are taken on the bit patterns.
+__global__ void __launch_bounds__(256) k_scalar_speed(const double *U, long long n, double inv_dx,
+                                                      double *speed, double *smax, int *status)
+{
+    unsigned long long m = 0, fl = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = __double_as_longlong(U[i]);
+        const unsigned long long a = (unsigned long long)(b & 0x7fffffffffffffffLL);
+        if (!below_1e300(U[i])) atomicOr(status, ST_NONPHYS_CELL);
+        m = m > a ? m : a;
+        if (a != 0) fl |= (b < 0) ? SGN_NEG : SGN_POS;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, m, o);
+        m = m > w ? m : w;
+        fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax((unsigned long long *)speed, m);
+        if (fl) atomicOr((unsigned long long *)(speed + 1), fl);
+        if (smax) {
+            const double s = __dmul_rn(__longlong_as_double((long long)m), inv_dx);
+            atomicMax((unsigned long long *)smax, (unsigned long long)__double_as_longlong(s));
+        }
+    }
+}
+
+cudaError_t launch_scalar_speed(const double *U, long long n, double inv_dx, double *speed,
+                                double *smax, int *status, cudaStream_t s)
+{
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_scalar_speed<<<(unsigned)blocks, 256, 0, s>>>(U, n, inv_dx, speed, smax, status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_alpha(int C, const AlphaArgs &a, cudaStream_t s)
@@ -255,6 +296,9 @@ static cudaError_t by_order(int R, Args &&...args)
 template <int R> struct AdvF {
     static cudaError_t run(const AdvArgs &a, cudaStream_t s) { return launch_advection<R>(a, s); }
 };
+template <int R> struct BurgF {
+    static cudaError_t run(const AdvArgs &a, cudaStream_t s) { return launch_burgers<R>(a, s); }
+};
 template <int R> struct E1F {
     static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler1d<R>(a, s); }
 };
@@ -292,6 +336,15 @@ static int valid_order(int R) { return R >= 5 && R <= 17 && (R % 2) == 1; }
 static enomr_status compute_alpha(enomr_ctx *c, const double *U, bool want_smax)
 {
     if (c->eq == ENOMR_ADVECTION) return ENOMR_OK;
+    if (c->eq == ENOMR_BURGERS) {
+        CU_TRY(cudaMemsetAsync(c->ax, 0, sizeof(double) * 2, c->stream));
+        if (want_smax) CU_TRY(cudaMemsetAsync(c->smax, 0, sizeof(double), c->stream));
+        prof_start(c, 3);
+        cudaError_t e = launch_scalar_speed(U, c->nx, 1.0 / c->dx, c->ax,
+                                            want_smax ? c->smax : nullptr, c->status, c->stream);
+        prof_stop(c, 3);
+        return cu(e);
+    }
     const int C = c->ndim == 2 ? 4 : 3;
     CU_TRY(cudaMemsetAsync(c->ax, 0, sizeof(double) * 3 * c->ny, c->stream));
     if (C == 4) CU_TRY(cudaMemsetAsync(c->ay, 0, sizeof(double) * 3 * c->nx, c->stream));
@@ -338,17 +391,19 @@ static SweepArgs sweep_args(enomr_ctx *c, const double *U, bool ysweep)
 static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilogue &epi,
                                       uint8_t *sel, double *ft = nullptr)
 {
-    if (c->eq == ENOMR_ADVECTION) {
+    if (c->eq == ENOMR_ADVECTION || c->eq == ENOMR_BURGERS) {
         AdvArgs a;
         a.U = U;
         a.n = c->nx;
         a.bc = c->bc;
         a.a = c->adv;
         a.inv_h = 1.0 / c->dx;
+        a.speed = c->ax;
         a.sel = sel;
         a.epi = epi;
         prof_start(c, 1);
-        cudaError_t e = by_order<AdvF>(c->order, a, c->stream);
+        cudaError_t e = c->eq == ENOMR_ADVECTION ? by_order<AdvF>(c->order, a, c->stream)
+                                                 : by_order<BurgF>(c->order, a, c->stream);
         prof_stop(c, 1);
         return cu(e);
     }
@@ -442,7 +497,8 @@ ENOMR_API enomr_status enomr_init(enomr_ctx **out, int eq, int ndim, int64_t nx,
     if (!out) return ENOMR_EINVAL;
     *out = nullptr;
     if (!valid_order(order)) return ENOMR_EINVAL;
-    if (eq != ENOMR_ADVECTION && eq != ENOMR_EULER) return ENOMR_EINVAL;
+    if (eq != ENOMR_ADVECTION && eq != ENOMR_EULER && eq != ENOMR_BURGERS) return ENOMR_EINVAL;
+    if (eq == ENOMR_BURGERS && ndim != 1) return ENOMR_EINVAL;
     if (bc != ENOMR_PERIODIC && bc != ENOMR_TRANSMISSIVE) return ENOMR_EINVAL;
     if (ndim != 1 && ndim != 2) return ENOMR_EINVAL;
     if (eq == ENOMR_ADVECTION && ndim != 1) return ENOMR_EINVAL;
@@ -469,7 +525,7 @@ ENOMR_API enomr_status enomr_init(enomr_ctx **out, int eq, int ndim, int64_t nx,
     c->gamma = gamma;
     c->adv = adv_speed;
     c->stream = (cudaStream_t)stream;
-    const int C = eq == ENOMR_ADVECTION ? 1 : (ndim == 2 ? 4 : 3);
+    const int C = eq != ENOMR_EULER ? 1 : (ndim == 2 ? 4 : 3);
     c->nstate = (long long)C * nx * ny;
     bool ok = cudaMalloc(&c->ax, sizeof(double) * 3 * ny) == cudaSuccess &&
               cudaMalloc(&c->ay, sizeof(double) * 3 * nx) == cudaSuccess &&
@@ -767,6 +823,7 @@ ENOMR_API enomr_status enomr_rhs_vjp(enomr_ctx *c, const double *U, const double
 {
     if (!c || !U || !Lbar || !Ubar || (const double *)Ubar == U || (const double *)Ubar == Lbar)
         return ENOMR_EINVAL;
+    if (c->eq == ENOMR_BURGERS) return ENOMR_EINVAL;
     if (!accumulate) CU_TRY(cudaMemsetAsync(Ubar, 0, sizeof(double) * c->nstate, c->stream));
     return rhs_vjp_impl(c, U, Lbar, Ubar, scale);
 }
@@ -775,6 +832,7 @@ ENOMR_API enomr_status enomr_step_vjp(enomr_ctx *c, const double *Un, double dt,
                                       const double *Ubar_np1, double *Ubar_n)
 {
     if (!c || !Un || !Ubar_np1 || !Ubar_n || !(dt > 0.0)) return ENOMR_EINVAL;
+    if (c->eq == ENOMR_BURGERS) return ENOMR_EINVAL;
     if ((const double *)Ubar_n == Ubar_np1 || (const double *)Ubar_n == Un) return ENOMR_EINVAL;
     enomr_status st;
     // recompute the stages from the step's checkpoint U^n

@@ -6,6 +6,20 @@
 
 namespace enomr {
 
+// x > 0 (+inf included, NaN excluded) and |x| < 1e300, tested on the
+// integer ALU: for doubles the IEEE bit pattern, read as an int64, orders
+// like the value on the non-negative half-line.
+__device__ __forceinline__ bool positive(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000LL;
+}
+
+__device__ __forceinline__ bool below_1e300(double x)
+{
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < 0x7e37e43c8800759cLL;
+}
+
 struct CellWaves {
     double u, v, c;  // normal and tangential velocity, sound speed
 };
@@ -28,7 +42,7 @@ __device__ __forceinline__ CellWaves cell_waves(double rho, double mx, double my
     const double v = (C == 4) ? __dmul_rn(my, ir) : 0.0;
     const double ke = (C == 4) ? __fma_rn(u, u, __dmul_rn(v, v)) : __dmul_rn(u, u);
     const double p = __dmul_rn(gm1, __fma_rn(-0.5 * rho, ke, E));
-    if (!(rho > 0.0) || !(p > 0.0) || !(fabs(E) < 1e300)) atomicOr(status, ST_NONPHYS_CELL);
+    if (!positive(rho) || !positive(p) || !below_1e300(E)) atomicOr(status, ST_NONPHYS_CELL);
     const double c2 = __dmul_rn(__dmul_rn(gamma, p), ir);
     CellWaves w;
     w.u = u;

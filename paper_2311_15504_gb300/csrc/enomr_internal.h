@@ -10,6 +10,9 @@ namespace enomr {
 // Status bits of the device status word.
 enum : int { ST_NONPHYS_CELL = 1, ST_NONPHYS_ROE = 2 };
 
+// Burgers sign flags (second word of AdvArgs::speed): some u < 0, some u > 0
+enum : unsigned long long { SGN_NEG = 1ULL, SGN_POS = 2ULL };
+
 // What a sweep does with its flux difference D_i = -(F_{i+1/2}-F_{i-1/2})/h.
 enum EpiMode : int {
     EPI_STORE = 0,   // out = D (+ Dprev)
@@ -45,6 +48,7 @@ struct AdvArgs {
     long long n;
     int bc;
     double a, inv_h;
+    const double *speed;   // Burgers: [max |u|, sign flags as bits] of U
     uint8_t *sel;          // optional [2][n+1]
     Epilogue epi;
 };
@@ -100,6 +104,7 @@ cudaError_t launch_batch_dt(const double *alpha, const double *inv_dx, double cf
                             double *dt, cudaStream_t s);
 
 template <int R> cudaError_t launch_advection(const AdvArgs &a, cudaStream_t s);
+template <int R> cudaError_t launch_burgers(const AdvArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler1d(const SweepArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, cudaStream_t s);
@@ -127,6 +132,8 @@ template <int R> cudaError_t launch_advection_vjp(const AdvArgs &a, const double
                                                   double *Ubar, double scale, cudaStream_t s);
 
 cudaError_t launch_alpha(int C, const AlphaArgs &a, cudaStream_t s);
+cudaError_t launch_scalar_speed(const double *U, long long n, double inv_dx, double *speed,
+                                double *smax, int *status, cudaStream_t s);
 cudaError_t launch_set_dt(const double *smax, double cfl, double dt_fixed, double *dt_dev,
                           cudaStream_t s);
 

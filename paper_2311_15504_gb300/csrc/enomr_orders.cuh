@@ -3,21 +3,26 @@
 // compile as separate translation units in parallel.
 #pragma once
 
-#include "enomr_kernels.cuh"
+#include "enomr_scalar.cuh"
+#include "enomr_sweep.cuh"
 #include "enomr_vjp.cuh"
 
 namespace enomr {
 
-// Tile shapes (interfaces per line x lines per CTA).
+// Interfaces per CTA of the scalar kernels (sweep tile shapes: enomr_sweep.cuh).
 constexpr int ADV_TP = 256;
-constexpr int E1_TP = 64;
-constexpr int X_TP = 128, X_NL = 2;
-constexpr int Y_TP = 64, Y_NL = 4;
 
 template <int R> cudaError_t launch_advection(const AdvArgs &a, cudaStream_t s)
 {
     const long long tiles = (a.n + ADV_TP - 2) / (ADV_TP - 1);
     k_advection<R, ADV_TP><<<(unsigned)tiles, ADV_TP, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t launch_burgers(const AdvArgs &a, cudaStream_t s)
+{
+    const long long tiles = (a.n + ADV_TP - 2) / (ADV_TP - 1);
+    k_burgers<R, ADV_TP><<<(unsigned)tiles, ADV_TP, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -45,6 +50,7 @@ template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, cudaStream_t s
 }
 
 template cudaError_t launch_advection<ENOMR_R>(const AdvArgs &, cudaStream_t);
+template cudaError_t launch_burgers<ENOMR_R>(const AdvArgs &, cudaStream_t);
 template cudaError_t launch_euler1d<ENOMR_R>(const SweepArgs &, cudaStream_t);
 template cudaError_t launch_euler2d_x<ENOMR_R>(const SweepArgs &, cudaStream_t);
 template cudaError_t launch_euler2d_y<ENOMR_R>(const SweepArgs &, cudaStream_t);

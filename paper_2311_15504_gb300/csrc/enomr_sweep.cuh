@@ -1,0 +1,358 @@
+// enomr_sweep.cuh -- Euler line sweeps (1D, and the x and y sweeps of 2D)
+// and the batched persistent 1D stage.
+//
+// arXiv 2311.15504: Sec. 2.1 (Eq. 1DWENOFD, Eq. LF_Flux_Split), Sec. 3.2,
+// Sec. 4 (Roe-averaged characteristic decomposition, Euler equations),
+// Eq. TVD3rdRK.
+//
+// Rows of L are scaled to carry a unit entry (the scheme is invariant to
+// such scalings, Sec. 3.3), so a projection costs 3 FMAs (1 for the shear
+// field) instead of 4; the 1/2 of the splitting and the row scalings are
+// folded into the back-projection.
+// Tiles: a CTA stages TP + 2g - 1 cells of NL lines (with their ghost cells,
+// wrapped or clamped) into shared memory together with primitive values
+// and physical fluxes, computes TP interface fluxes per line (one per
+// thread) and updates the TP - 1 cells between them; neighbouring tiles
+// overlap by one interface.
+#pragma once
+
+#include "enomr_kernels.cuh"
+
+namespace enomr {
+
+// Tile shapes of the sweeps (interfaces per line x lines per CTA).
+constexpr int E1_TP = 64;
+constexpr int X_TP = 128, X_NL = 2;
+constexpr int Y_TP = 64, Y_NL = 4;
+
+// ---------------------------------------------------------------------------
+// Euler line sweep.  DIR 0: lines are rows (x contiguous); DIR 1: lines are
+// columns.  C = 3 (1D) or 4 (2D, components rho, m_x, m_y, E).
+// ---------------------------------------------------------------------------
+template <int R, int C, int TP, int NL>
+struct SweepSmem {
+    static constexpr int g = (R + 1) / 2, S = TP + 2 * g - 1;
+    double sU[C][NL][S];
+    double sF[C][NL][S];
+    double sP[4][NL][S];  // sqrt(rho), u_n, u_t, H
+    double sFh[C][NL][TP];
+    unsigned long long red[TP * NL / 32][3];
+};
+
+// One tile: NL lines x TP interfaces starting at interface x0 of line l0.
+// All threads of the CTA must call it; it ends after its epilogue.
+template <int R, int C, int DIR, int TP, int NL>
+__device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, long long l0,
+                                           const double *sA, SweepSmem<R, C, TP, NL> &sm)
+{
+    constexpr int g = (R + 1) / 2, W = 2 * g - 1, S = TP + 2 * g - 1, T = Tab<R>::T;
+    constexpr int NT = TP * NL;
+    constexpr int QN = (DIR == 0) ? 1 : 2;  // normal momentum component
+    constexpr int QT = (DIR == 0) ? 2 : 1;  // tangential momentum component (C = 4)
+    auto &sU = sm.sU;
+    auto &sF = sm.sF;
+    auto &sP = sm.sP;
+    auto &sFh = sm.sFh;
+
+    const long long nx = A.nx, ny = A.ny, ncell = nx * ny;
+    const long long nlen = (DIR == 0) ? nx : ny;
+    const long long nlines = (DIR == 0) ? ny : nx;
+    const int tid = threadIdx.x;
+
+    // ---- stage cells, primitives and physical fluxes (normal direction)
+    for (int idx = tid; idx < NL * S; idx += NT) {
+        int line, s;
+        if (DIR == 0) {
+            line = idx / S;
+            s = idx - line * S;
+        } else {
+            s = idx / NL;
+            line = idx - s * NL;
+        }
+        long long L = l0 + line;
+        if (L >= nlines) L = nlines - 1;
+        const long long cell = ghost(x0 - g + s, nlen, A.bc);
+        const long long gi = (DIR == 0) ? L * nx + cell : cell * nx + L;
+        double u[C];
+#pragma unroll
+        for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
+        const StagedCell<C> sc_ = stage_cell<C>(u[0], u[QN], (C == 4) ? u[QT] : 0.0, u[C - 1], A.gm1);
+        if (!positive(u[0]) || !positive(sc_.p) || !below_1e300(u[C - 1]))
+            atomicOr(A.status, ST_NONPHYS_CELL);
+        sU[0][line][s] = u[0];
+        sU[1][line][s] = u[QN];
+        if (C == 4) sU[2][line][s] = u[QT];
+        sU[C - 1][line][s] = u[C - 1];
+#pragma unroll
+        for (int q = 0; q < C; ++q) sF[q][line][s] = sc_.F[q];
+        sP[0][line][s] = sc_.sq;
+        sP[1][line][s] = sc_.un;
+        sP[2][line][s] = sc_.ut;
+        sP[3][line][s] = sc_.H;
+    }
+    __syncthreads();
+
+    // ---- one interface per thread
+    int p, line;
+    if (DIR == 0) {
+        p = tid % TP;
+        line = tid / TP;
+    } else {
+        line = tid % NL;
+        p = tid / NL;
+    }
+    const long long Lg = l0 + line;
+    const long long k = x0 + p;  // interface x_{k-1/2}, cells k-1 | k
+    const bool valid = (Lg < nlines) && (k <= nlen);
+    const int sl = p + g - 1, sr = p + g;
+
+    // Roe average (Sec. 4); for two bitwise-equal states it is that state.
+    bool eqLR = true;
+#pragma unroll
+    for (int q = 0; q < C; ++q)
+        eqLR = eqLR && (__double_as_longlong(sU[q][line][sl]) == __double_as_longlong(sU[q][line][sr]));
+    const RoeFace rf = roe_face(eqLR, sP[0][line][sl], sP[1][line][sl], sP[2][line][sl],
+                                sP[3][line][sl], sP[0][line][sr], sP[1][line][sr],
+                                sP[2][line][sr], sP[3][line][sr], C == 4, A.gm1, A.inv_gm1);
+    if (valid && !positive(rf.c2)) atomicOr(A.status, ST_NONPHYS_ROE);
+    const double uh = rf.uh, vh = rf.vh, Hh = rf.Hh, hq = rf.hq, cs = rf.cs, kap = rf.kap,
+                 c2g = rf.c2g, b1 = rf.b1;
+
+    const double *al = A.alpha + 3 * (Lg < nlines ? Lg : nlines - 1);
+    const double a_m = al[0], a_0 = al[1], a_p = al[2];
+
+    // Back-projection accumulators.  With phi_f = s_f (f^+ + f^-)_f and the
+    // inverse row scalings s = (b1/4, -b1/2, [1/2,] b1/4) (the 1/2 of the
+    // splitting included), F = R phi reads
+    //   F0 = (phi_0 + phi_a) + phi_1,   F1 = u F0 + c (phi_a - phi_0),
+    //   F2 = v F0 + phi_2 (2D),         FE = H (phi_0 + phi_a) + u c (phi_a - phi_0)
+    //                                        + hq phi_1 + v phi_2,
+    // phi_a being the u+c field.
+    double acc_s = 0.0, acc_d = 0.0, ph1 = 0.0, ph2 = 0.0;
+
+    // Scaled left-eigenvector row of field f (a unit entry on E, or on the
+    // tangential momentum for the shear field) and the split speed alpha_f.
+    auto row = [&](int f, double &l0c, double &l1c, double &alpha) {
+        if (C == 4 && f == 2) {
+            l0c = -vh;
+            l1c = 0.0;
+            alpha = a_0;
+        } else if (f == 0) {
+            l0c = fma(uh, kap, hq);
+            l1c = -(uh + kap);
+            alpha = a_m;
+        } else if (f == C - 1) {
+            l0c = fma(-uh, kap, hq);
+            l1c = -(uh - kap);
+            alpha = a_p;
+        } else {
+            l0c = hq - c2g;
+            l1c = -uh;
+            alpha = a_0;
+        }
+    };
+    // w = l U and q = l F of staged cell s (the same operations on every path).
+    auto project = [&](int f, int s, double l0c, double l1c, double &w, double &q) {
+        if (C == 4 && f == 2) {
+            w = fma(l0c, sU[0][line][s], sU[2][line][s]);
+            q = fma(l0c, sF[0][line][s], sF[2][line][s]);
+        } else {
+            w = sU[C - 1][line][s];
+            q = sF[C - 1][line][s];
+            if (C == 4) {
+                w = fma(-vh, sU[2][line][s], w);
+                q = fma(-vh, sF[2][line][s], q);
+            }
+            w = fma(l1c, sU[1][line][s], w);
+            q = fma(l1c, sF[1][line][s], q);
+            w = fma(l0c, sU[0][line][s], w);
+            q = fma(l0c, sF[0][line][s], q);
+        }
+    };
+    auto accumulate = [&](int f, double ft) {
+        if (f == 0) {
+            const double ph = 0.25 * b1 * ft;
+            acc_s += ph;
+            acc_d -= ph;
+        } else if (f == C - 1) {
+            const double ph = 0.25 * b1 * ft;
+            acc_s += ph;
+            acc_d += ph;
+        } else if (C == 4 && f == 2) {
+            ph2 = 0.5 * ft;
+        } else {
+            ph1 = -0.5 * b1 * ft;
+        }
+    };
+
+    // Flat windows.  If the states of three consecutive cells ending or
+    // starting at a side's centre are bitwise equal, every field's projected
+    // values there are bitwise equal too, so that side's IS_0 is exactly 0,
+    // no candidate is tested and minmod returns v(0): only the centre cell
+    // needs projecting.  The result is the same as on the full path.
+    auto same = [&](int a, int b) {
+        bool e = true;
+#pragma unroll
+        for (int q = 0; q < C; ++q)
+            e = e && (__double_as_longlong(sU[q][line][a]) == __double_as_longlong(sU[q][line][b]));
+        return e;
+    };
+    const bool e0 = same(sl - 2, sl - 1), e1 = same(sl - 1, sl), e2 = same(sl, sr),
+               e3 = same(sr, sr + 1), e4 = same(sr + 1, sr + 2);
+    const bool plus_flat = (e0 && e1) || (e2 && e3);   // centre cell k-1
+    const bool minus_flat = (e3 && e4) || (e1 && e2);  // centre cell k (mirrored)
+    const bool flat = plus_flat && minus_flat;
+
+    if (__all_sync(FULL, flat || !valid)) {
+        // e2: the two centre states are bitwise equal, so are their
+        // projections; the second one is not recomputed.
+#pragma unroll
+        for (int f = 0; f < C; ++f) {
+            double l0c, l1c, alpha, w, q;
+            row(f, l0c, l1c, alpha);
+            project(f, sl, l0c, l1c, w, q);
+            const double fp = fma(alpha, w, q);
+            if (!e2) project(f, sr, l0c, l1c, w, q);
+            const double fm = fma(-alpha, w, q);
+            accumulate(f, fp + fm);
+            if (A.sel && valid) {
+                const long long NI = nlen + 1;
+                A.sel[((0 * C + f) * nlines + Lg) * NI + k] = (uint8_t)(T + 2);
+                A.sel[((1 * C + f) * nlines + Lg) * NI + k] = (uint8_t)(T + 2);
+            }
+            if (A.ft_out && valid) A.ft_out[(f * nlines + Lg) * (nlen + 1) + k] = fp + fm;
+        }
+    } else {
+#pragma unroll 1
+        for (int f = 0; f < C; ++f) {
+            double l0c, l1c, alpha;
+            row(f, l0c, l1c, alpha);
+            double vp[W], vm[W];
+#pragma unroll
+            for (int j = 0; j < 2 * g; ++j) {
+                double w, q;
+                project(f, p + j, l0c, l1c, w, q);
+                if (j <= 2 * g - 2) vp[j] = fma(alpha, w, q);       // cell k-1+l, l = j-(g-1)
+                if (j >= 1) vm[2 * g - 1 - j] = fma(-alpha, w, q);  // cell k-l,   l = g-j
+            }
+            int selp, selm;
+            const double fp = mr_value<R>(vp, sA, valid, selp);
+            const double fm = mr_value<R>(vm, sA, valid, selm);
+            accumulate(f, fp + fm);
+            if (A.sel && valid) {
+                const long long NI = nlen + 1;
+                A.sel[((0 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selp;
+                A.sel[((1 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selm;
+            }
+            if (A.ft_out && valid) A.ft_out[(f * nlines + Lg) * (nlen + 1) + k] = fp + fm;
+        }
+    }
+    double Fh[C];
+    Fh[0] = acc_s + ph1;
+    Fh[1] = fma(uh, Fh[0], cs * acc_d);
+    if (C == 4) Fh[2] = fma(vh, Fh[0], ph2);
+    Fh[C - 1] = fma(Hh, acc_s, fma(uh * cs, acc_d, fma(hq, ph1, vh * ph2)));
+#pragma unroll
+    for (int q = 0; q < C; ++q) sFh[q][line][p] = Fh[q];
+    __syncthreads();
+
+    // ---- flux difference and epilogue for the TP-1 cells of the tile
+    unsigned long long ws[3] = {0, 0, 0};
+    if (p < TP - 1 && Lg < nlines) {
+        const long long i = x0 + p;
+        if (i < nlen) {
+            const long long gi = (DIR == 0) ? Lg * nx + i : i * nx + Lg;
+            const int sc = p + g;  // staged index of cell i
+            double o[C];
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+                // map line component back to the state component
+                const int qs = (q == 1) ? QN : ((C == 4 && q == 2) ? QT : q);
+                const double D = -(sFh[q][line][p + 1] - sFh[q][line][p]) * A.inv_h;
+                o[q] = epilogue(A.epi, qs * ncell + gi, D, sU[q][line][sc]);
+            }
+            if (C == 3 && A.alpha_next) {
+                double w3[3];
+                wave_speeds3(o[0], o[1], o[2], A.gm1, A.gamma, w3, A.status);
+#pragma unroll
+                for (int k3 = 0; k3 < 3; ++k3) ws[k3] = __double_as_longlong(w3[k3]);
+            }
+        }
+    }
+    if (C == 3 && A.alpha_next) {
+        // CTA maximum of the new state's wave speeds -> the next stage's alpha
+#pragma unroll
+        for (int k3 = 0; k3 < 3; ++k3) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long w = __shfl_xor_sync(FULL, ws[k3], o);
+                ws[k3] = ws[k3] > w ? ws[k3] : w;
+            }
+        }
+        if ((tid & 31) == 0)
+            for (int k3 = 0; k3 < 3; ++k3) sm.red[tid >> 5][k3] = ws[k3];
+        __syncthreads();
+        if (tid < 3) {
+            unsigned long long m = 0;
+            for (int wi = 0; wi < NT / 32; ++wi) m = m > sm.red[wi][tid] ? m : sm.red[wi][tid];
+            atomicMax((unsigned long long *)(A.alpha_next + tid), m);
+        }
+    }
+}
+
+template <int R, int C, int DIR, int TP, int NL>
+__global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
+{
+    constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
+    __shared__ SweepSmem<R, C, TP, NL> sm;
+    __shared__ double sA[T * W];
+    load_a_table<R>(sA, threadIdx.x, TP * NL);
+    const long long x0 = (long long)((DIR == 0) ? blockIdx.x : blockIdx.y) * (TP - 1);
+    const long long l0 = (long long)((DIR == 0) ? blockIdx.y : blockIdx.x) * NL;
+    sweep_tile<R, C, DIR, TP, NL>(A, x0, l0, sA, sm);
+}
+
+// ---------------------------------------------------------------------------
+// Batched 1D Euler: one persistent launch per RK stage over a table of
+// (problem, first interface) tiles of many independent problems of uneven
+// size.  Each tile runs the same interface arithmetic as the single-problem
+// sweep, so results are bitwise those of one problem at a time.
+// ---------------------------------------------------------------------------
+template <int R, int TP>
+__global__ void __launch_bounds__(TP) k_batch_stage(BatchArgs B)
+{
+    constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
+    __shared__ SweepSmem<R, 3, TP, 1> sm;
+    __shared__ double sA[T * W];
+    load_a_table<R>(sA, threadIdx.x, TP);
+    for (long long t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
+        __syncthreads();  // the previous tile is done with shared memory
+        const BatchTile tl = B.tiles[t];
+        const int pr = tl.prob;
+        const long long base = B.base[pr];
+        SweepArgs A;
+        A.U = B.Us + base;
+        A.nx = B.n[pr];
+        A.ny = 1;
+        A.bc = B.bc;
+        A.gm1 = B.gm1;
+        A.inv_gm1 = B.inv_gm1;
+        A.gamma = B.gamma;
+        A.inv_h = B.inv_dx[pr];
+        A.alpha = B.alpha + 3 * pr;
+        A.alpha_next = B.alpha_next ? B.alpha_next + 3 * pr : nullptr;
+        A.sel = nullptr;
+        A.ft_out = nullptr;
+        A.status = B.status;
+        A.epi.mode = EPI_STAGE;
+        A.epi.c0 = B.c0;
+        A.epi.c1 = B.c1;
+        A.epi.dt_dev = B.dt + pr;
+        A.epi.Un = B.Un + base;
+        A.epi.Dprev = nullptr;
+        A.epi.out = B.out + base;
+        sweep_tile<R, 3, 0, TP, 1>(A, tl.x0, 0, sA, sm);
+    }
+}
+
+}  // namespace enomr

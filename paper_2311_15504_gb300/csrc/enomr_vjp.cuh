@@ -16,7 +16,7 @@
 // frozen argmax cell by k_alpha_vjp.
 #pragma once
 
-#include "enomr_kernels.cuh"
+#include "enomr_sweep.cuh"
 
 namespace enomr {
 

@@ -14,7 +14,7 @@ import os
 
 import torch
 
-ADVECTION, EULER = 0, 1
+ADVECTION, EULER, BURGERS = 0, 1, 2
 PERIODIC, TRANSMISSIVE = 0, 1
 ORDERS = (5, 7, 9, 11, 13, 15, 17)
 
@@ -93,9 +93,9 @@ def probe_fp64_fma(iters: int = 20000, device=None):
 class Solver:
     """One ENO-MR problem on one GPU.
 
-    eq: ADVECTION (1D, f = adv_speed * u) or EULER (1D: shape = nx, state
-    [3, nx]; 2D: shape = (ny, nx), state [4, ny, nx]).  States are float64
-    CUDA tensors, contiguous.
+    eq: ADVECTION (1D, f = adv_speed * u), BURGERS (1D, f = u^2/2) or EULER
+    (1D: shape = nx, state [3, nx]; 2D: shape = (ny, nx), state
+    [4, ny, nx]).  States are float64 CUDA tensors, contiguous.
     """
 
     def __init__(self, eq, shape, order=9, dx=1.0, dy=None, bc=TRANSMISSIVE, gamma=1.4,
@@ -109,9 +109,9 @@ class Solver:
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.type != "cuda":
             raise ValueError("the ENO-MR solver runs on CUDA devices only")
-        self.ncomp = 1 if eq == ADVECTION else (4 if ndim == 2 else 3)
-        self.state_shape = ((nx,) if eq == ADVECTION else
-                            ((3, nx) if ndim == 1 else (4, ny, nx)))
+        scalar = eq in (ADVECTION, BURGERS)
+        self.ncomp = 1 if scalar else (4 if ndim == 2 else 3)
+        self.state_shape = ((nx,) if scalar else ((3, nx) if ndim == 1 else (4, ny, nx)))
         ctx = _P()
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream(self.device).cuda_stream
@@ -135,7 +135,7 @@ class Solver:
         return _P(U.data_ptr())
 
     def n_sel(self):
-        if self.eq == ADVECTION:
+        if self.eq in (ADVECTION, BURGERS):
             return 2 * (self.nx + 1)
         if self.ndim == 1:
             return 6 * (self.nx + 1)

@@ -135,3 +135,22 @@ def euler_scale_fn(line_state, n_lines, nlen, R, bc, alpha, gamma=1.4):
             best = max(best, float(m))
         return best
     return fn
+
+
+def shock_gate(step_fn, U0, steps, seeds=(1, 2)):
+    """Rounding-sensitivity envelope of the oracle itself: the L1 distance
+    between its trajectory and the same trajectory with a one-ulp random
+    perturbation after the first step (largest over seeds).  The shock-case
+    gate is max(1e-6, 4 * envelope)."""
+    base = U0.copy()
+    for dt in steps:
+        base = step_fn(base, dt)
+    env = 0.0
+    for sd in seeds:
+        rng = np.random.Generator(np.random.PCG64(sd))
+        b = step_fn(U0.copy(), steps[0])
+        b = b + np.spacing(np.abs(b)) * rng.choice([-1, 0, 1], size=b.shape)
+        for dt in steps[1:]:
+            b = step_fn(b, dt)
+        env = max(env, float(np.abs(b - base).mean()))
+    return base, max(1e-6, 4.0 * env), env

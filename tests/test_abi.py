@@ -54,6 +54,9 @@ def test_host_side_argument_checks(lib):
         (1, 2, 64, 4, 0.1, 0.1, 9, 1.4, 0, 1.0),     # periodic needs ny >= 2g
         (1, 1, 100, 1, 0.1, 0.1, 5, 1.4, 7, 1.0),    # unknown bc
         (3, 1, 100, 1, 0.1, 0.1, 5, 1.4, 0, 1.0),    # unknown equation
+        (2, 2, 100, 100, 0.1, 0.1, 5, 1.4, 0, 1.0),  # Burgers is 1D
+        (0, 1, 0, 1, 0.1, 0.1, 5, 1.4, 1, 1.0),      # empty line
+        (1, 2, 0, 64, 0.1, 0.1, 5, 1.4, 1, 1.0),     # empty grid
     ]
     for args in bad:
         st = L.enomr_init(ctypes.byref(ctx), *args, P(0))

@@ -94,6 +94,41 @@ def test_advection_2p24(E, R):
     assert_values(got, forced, np.abs(u).max() / h, f"advection 2^24 R={R}")
 
 
+@pytest.mark.parametrize("R", [5, 9, 17])
+def test_burgers_2p24(E, R):
+    """Burgers at the throughput size (N = 2^24, [0, 2] periodic,
+    u0 = 1 + 0.5 sin^3(pi x) advanced 3 CFL steps).  u' has double zeros at
+    x = 0 and 1, where the indicators of hundreds of cells are at rounding
+    level; every flip is classified as a near-tie on its window (u > 0, so
+    the f^+ windows are f = u^2/2 at consecutive cells, as the oracle forms
+    them)."""
+    import torch
+    N = 1 << 24
+    u, h = wl.burgers_sine3(N)
+    s = E.Solver(E.BURGERS, N, order=R, dx=h, bc=E.PERIODIC)
+    ud = torch.from_numpy(u).cuda()
+    for _ in range(3):
+        s.step(ud, 0.0, 0.5)
+    u = ud.cpu().numpy()
+    assert u.min() > 0
+    sel = s.selection(ud).cpu().numpy()
+    got = s.rhs(ud).cpu().numpy()
+    s.check_status()
+    ref = oracle.rhs_burgers(u, h, R, want_sel=True)
+    rs = ref["sel"].reshape(-1)
+    flips = np.nonzero(rs != sel)[0]
+    print(f"burgers 2^24 R={R}: {flips.size} flips")
+    assert flips.size <= 1e-3 * sel.size
+    assert (flips < N + 1).all()  # f^- = 0: its windows cannot flip
+    if flips.size:
+        g = (R + 1) // 2
+        f = 0.5 * (u * u)
+        cells = (flips[:, None] - 1 + np.arange(-(g - 1), g)[None, :]) % N
+        assert_selection(R, sel[flips], rs[flips], f[cells], f"burgers 2^24 R={R}")
+    forced = oracle.rhs_burgers(u, h, R, forced=sel)["rhs"]
+    assert_values(got, forced, 0.5 * np.abs(u).max() ** 2 / h, f"burgers 2^24 R={R}")
+
+
 @pytest.mark.parametrize("R", [5, 17])
 def test_euler1d_6400(E, R):
     import torch

@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import assert_selection, assert_values, euler_flux_scale, euler_scale_fn
+from parity import (assert_selection, assert_values, euler_flux_scale, euler_scale_fn,
+                    shock_gate)
 from paper_2311_15504_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -141,25 +142,6 @@ def test_stage_and_step_match_oracle(E):
     s.stage(3, Un, U2, U3, dt)
     assert torch.equal(U3, Ud)
     s.check_status()
-
-
-def shock_gate(step_fn, U0, steps, seeds=(1, 2)):
-    """Rounding-sensitivity envelope of the oracle itself: the L1 distance
-    between its trajectory and the same trajectory with a one-ulp random
-    perturbation after the first step (largest over seeds).  The shock-case
-    gate is max(1e-6, 4 * envelope)."""
-    base = U0.copy()
-    for dt in steps:
-        base = step_fn(base, dt)
-    env = 0.0
-    for sd in seeds:
-        rng = np.random.Generator(np.random.PCG64(sd))
-        b = step_fn(U0.copy(), steps[0])
-        b = b + np.spacing(np.abs(b)) * rng.choice([-1, 0, 1], size=b.shape)
-        for dt in steps[1:]:
-            b = step_fn(b, dt)
-        env = max(env, float(np.abs(b - base).mean()))
-    return base, max(1e-6, 4.0 * env), env
 
 
 @pytest.mark.parametrize("R", [5, 7, 9])
