@@ -37,73 +37,30 @@ struct SweepSmem {
     double sP[4][NL][S];  // sqrt(rho), u_n, u_t, H
     double sFh[C][NL][TP];
     unsigned long long red[TP * NL / 32][3];
+    int list[TP * NL];  // interfaces (line * TP + p) that take the long path
+    int nlist;
 };
 
-// One tile: NL lines x TP interfaces starting at interface x0 of line l0.
-// All threads of the CTA must call it; it ends after its epilogue.
-template <int R, int C, int DIR, int TP, int NL>
-__device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, long long l0,
-                                           const double *sA, SweepSmem<R, C, TP, NL> &sm)
+// Flux of interface x_{k-1/2}, k = x0 + p, of tile line `line` into
+// sm.sFh[.][line][p] (and the selections / field values when requested).
+// FLATP: the interface is flat (both sides' centre triples of cell states
+// are bitwise equal), e2: its two centre states are bitwise equal.  The
+// long path (FLATP false) holds warp votes: all 32 lanes of the warp call
+// it together, lanes with valid == false only vote.
+template <int R, int C, int DIR, int TP, int NL, bool FLATP>
+__device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0, long long l0,
+                                               const double *sA, SweepSmem<R, C, TP, NL> &sm,
+                                               int p, int line, bool valid, bool e2)
 {
-    constexpr int g = (R + 1) / 2, W = 2 * g - 1, S = TP + 2 * g - 1, T = Tab<R>::T;
-    constexpr int NT = TP * NL;
-    constexpr int QN = (DIR == 0) ? 1 : 2;  // normal momentum component
-    constexpr int QT = (DIR == 0) ? 2 : 1;  // tangential momentum component (C = 4)
+    constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
     auto &sU = sm.sU;
     auto &sF = sm.sF;
     auto &sP = sm.sP;
     auto &sFh = sm.sFh;
-
-    const long long nx = A.nx, ny = A.ny, ncell = nx * ny;
-    const long long nlen = (DIR == 0) ? nx : ny;
-    const long long nlines = (DIR == 0) ? ny : nx;
-    const int tid = threadIdx.x;
-
-    // ---- stage cells, primitives and physical fluxes (normal direction)
-    for (int idx = tid; idx < NL * S; idx += NT) {
-        int line, s;
-        if (DIR == 0) {
-            line = idx / S;
-            s = idx - line * S;
-        } else {
-            s = idx / NL;
-            line = idx - s * NL;
-        }
-        long long L = l0 + line;
-        if (L >= nlines) L = nlines - 1;
-        const long long cell = ghost(x0 - g + s, nlen, A.bc);
-        const long long gi = (DIR == 0) ? L * nx + cell : cell * nx + L;
-        double u[C];
-#pragma unroll
-        for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
-        const StagedCell<C> sc_ = stage_cell<C>(u[0], u[QN], (C == 4) ? u[QT] : 0.0, u[C - 1], A.gm1);
-        if (!positive(u[0]) || !positive(sc_.p) || !below_1e300(u[C - 1]))
-            atomicOr(A.status, ST_NONPHYS_CELL);
-        sU[0][line][s] = u[0];
-        sU[1][line][s] = u[QN];
-        if (C == 4) sU[2][line][s] = u[QT];
-        sU[C - 1][line][s] = u[C - 1];
-#pragma unroll
-        for (int q = 0; q < C; ++q) sF[q][line][s] = sc_.F[q];
-        sP[0][line][s] = sc_.sq;
-        sP[1][line][s] = sc_.un;
-        sP[2][line][s] = sc_.ut;
-        sP[3][line][s] = sc_.H;
-    }
-    __syncthreads();
-
-    // ---- one interface per thread
-    int p, line;
-    if (DIR == 0) {
-        p = tid % TP;
-        line = tid / TP;
-    } else {
-        line = tid % NL;
-        p = tid / NL;
-    }
+    const long long nlen = (DIR == 0) ? A.nx : A.ny;
+    const long long nlines = (DIR == 0) ? A.ny : A.nx;
     const long long Lg = l0 + line;
     const long long k = x0 + p;  // interface x_{k-1/2}, cells k-1 | k
-    const bool valid = (Lg < nlines) && (k <= nlen);
     const int sl = p + g - 1, sr = p + g;
 
     // Roe average (Sec. 4); for two bitwise-equal states it is that state.
@@ -185,25 +142,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
         }
     };
 
-    // Flat windows.  If the states of three consecutive cells ending or
-    // starting at a side's centre are bitwise equal, every field's projected
-    // values there are bitwise equal too, so that side's IS_0 is exactly 0,
-    // no candidate is tested and minmod returns v(0): only the centre cell
-    // needs projecting.  The result is the same as on the full path.
-    auto same = [&](int a, int b) {
-        bool e = true;
-#pragma unroll
-        for (int q = 0; q < C; ++q)
-            e = e && (__double_as_longlong(sU[q][line][a]) == __double_as_longlong(sU[q][line][b]));
-        return e;
-    };
-    const bool e0 = same(sl - 2, sl - 1), e1 = same(sl - 1, sl), e2 = same(sl, sr),
-               e3 = same(sr, sr + 1), e4 = same(sr + 1, sr + 2);
-    const bool plus_flat = (e0 && e1) || (e2 && e3);   // centre cell k-1
-    const bool minus_flat = (e3 && e4) || (e1 && e2);  // centre cell k (mirrored)
-    const bool flat = plus_flat && minus_flat;
-
-    if (__all_sync(FULL, flat || !valid)) {
+    if (FLATP) {
         // e2: the two centre states are bitwise equal, so are their
         // projections; the second one is not recomputed.
 #pragma unroll
@@ -252,9 +191,127 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
     Fh[1] = fma(uh, Fh[0], cs * acc_d);
     if (C == 4) Fh[2] = fma(vh, Fh[0], ph2);
     Fh[C - 1] = fma(Hh, acc_s, fma(uh * cs, acc_d, fma(hq, ph1, vh * ph2)));
+    // a lane without an interface of its own (it only votes) must not store
+    // over the owner's slot
+    if (valid)
 #pragma unroll
-    for (int q = 0; q < C; ++q) sFh[q][line][p] = Fh[q];
+        for (int q = 0; q < C; ++q) sFh[q][line][p] = Fh[q];
+}
+
+// One tile: NL lines x TP interfaces starting at interface x0 of line l0.
+// All threads of the CTA must call it; it ends after its epilogue.
+template <int R, int C, int DIR, int TP, int NL>
+__device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, long long l0,
+                                           const double *sA, SweepSmem<R, C, TP, NL> &sm)
+{
+    constexpr int g = (R + 1) / 2, S = TP + 2 * g - 1;
+    constexpr int NT = TP * NL;
+    constexpr int QN = (DIR == 0) ? 1 : 2;  // normal momentum component
+    constexpr int QT = (DIR == 0) ? 2 : 1;  // tangential momentum component (C = 4)
+    auto &sU = sm.sU;
+    auto &sF = sm.sF;
+    auto &sP = sm.sP;
+    auto &sFh = sm.sFh;
+
+    const long long nx = A.nx, ny = A.ny, ncell = nx * ny;
+    const long long nlen = (DIR == 0) ? nx : ny;
+    const long long nlines = (DIR == 0) ? ny : nx;
+    const int tid = threadIdx.x;
+
+    if (tid == 0) sm.nlist = 0;
+    // ---- stage cells, primitives and physical fluxes (normal direction)
+    for (int idx = tid; idx < NL * S; idx += NT) {
+        int line, s;
+        if (DIR == 0) {
+            line = idx / S;
+            s = idx - line * S;
+        } else {
+            s = idx / NL;
+            line = idx - s * NL;
+        }
+        long long L = l0 + line;
+        if (L >= nlines) L = nlines - 1;
+        const long long cell = ghost(x0 - g + s, nlen, A.bc);
+        const long long gi = (DIR == 0) ? L * nx + cell : cell * nx + L;
+        double u[C];
+#pragma unroll
+        for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
+        const StagedCell<C> sc_ = stage_cell<C>(u[0], u[QN], (C == 4) ? u[QT] : 0.0, u[C - 1], A.gm1);
+        if (!positive(u[0]) || !positive(sc_.p) || !below_1e300(u[C - 1]))
+            atomicOr(A.status, ST_NONPHYS_CELL);
+        sU[0][line][s] = u[0];
+        sU[1][line][s] = u[QN];
+        if (C == 4) sU[2][line][s] = u[QT];
+        sU[C - 1][line][s] = u[C - 1];
+#pragma unroll
+        for (int q = 0; q < C; ++q) sF[q][line][s] = sc_.F[q];
+        sP[0][line][s] = sc_.sq;
+        sP[1][line][s] = sc_.un;
+        sP[2][line][s] = sc_.ut;
+        sP[3][line][s] = sc_.H;
+    }
     __syncthreads();
+
+    // ---- interface fluxes.  A flat interface (see below) is evaluated by
+    // its own thread; the others are appended to a list and evaluated by
+    // whole warps, 32 list entries at a time, so that the long path (whose
+    // candidate walk is warp-uniform) runs without idle lanes.
+    {
+        int p, line;
+        if (DIR == 0) {
+            p = tid % TP;
+            line = tid / TP;
+        } else {
+            line = tid % NL;
+            p = tid / NL;
+        }
+        const bool valid = (l0 + line < nlines) && (x0 + p <= nlen);
+        const int sl = p + g - 1, sr = p + g;
+        // Flat windows.  If the states of three consecutive cells ending or
+        // starting at a side's centre are bitwise equal, every field's
+        // projected values there are bitwise equal too, so that side's IS_0
+        // is exactly 0, no candidate is tested and minmod returns v(0): only
+        // the centre cell needs projecting.  The result is the same as on
+        // the long path.
+        auto same = [&](int a, int b) {
+            bool e = true;
+#pragma unroll
+            for (int q = 0; q < C; ++q)
+                e = e && (__double_as_longlong(sU[q][line][a]) == __double_as_longlong(sU[q][line][b]));
+            return e;
+        };
+        const bool e0 = same(sl - 2, sl - 1), e1 = same(sl - 1, sl), e2 = same(sl, sr),
+                   e3 = same(sr, sr + 1), e4 = same(sr + 1, sr + 2);
+        const bool plus_flat = (e0 && e1) || (e2 && e3);   // centre cell k-1
+        const bool minus_flat = (e3 && e4) || (e1 && e2);  // centre cell k (mirrored)
+        const bool flat = plus_flat && minus_flat;
+        if (valid && flat)
+            interface_flux<R, C, DIR, TP, NL, true>(A, x0, l0, sA, sm, p, line, true, e2);
+        // append the other valid interfaces, in lane order within each warp
+        const unsigned need = __ballot_sync(FULL, valid && !flat);
+        if (need) {
+            const int lane = tid & 31;
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&sm.nlist, __popc(need));
+            base = __shfl_sync(FULL, base, 0);
+            if ((need >> lane) & 1u) sm.list[base + __popc(need & ((1u << lane) - 1u))] = line * TP + p;
+        }
+    }
+    __syncthreads();
+    {
+        const int n = sm.nlist;
+        for (int base = tid & ~31; base < n; base += NT) {
+            const int t = base + (tid & 31);
+            const bool act = t < n;
+            const int e = sm.list[act ? t : base];
+            interface_flux<R, C, DIR, TP, NL, false>(A, x0, l0, sA, sm, e % TP, e / TP, act, false);
+        }
+    }
+    __syncthreads();
+
+    const int p = (DIR == 0) ? tid % TP : tid / NL;
+    const int line = (DIR == 0) ? tid / TP : tid % NL;
+    const long long Lg = l0 + line;
 
     // ---- flux difference and epilogue for the TP-1 cells of the tile
     unsigned long long ws[3] = {0, 0, 0};
