@@ -29,6 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 EQ_ADVECTION, EQ_EULER1D, EQ_EULER2D, EQ_BURGERS = 0, 1, 2, 3
+SIDE_TRANSMISSIVE, SIDE_REFLECTIVE, SIDE_INFLOW = 1, 2, 3
 BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
 ORC_OK, ORC_EINVAL, ORC_ENONPHYS = 0, 1, 4
 
@@ -71,6 +72,8 @@ def _load():
                 "orc_mr_indicators": (I, [I, P, P, P, P, P]),
                 "orc_rhs_advection": (I, [L, P, D, I, I, D, P, P, P, P, P]),
                 "orc_rhs_burgers": (I, [L, P, D, I, I, P, P, P, P, P]),
+                "orc_rhs_euler2d_ext": (I, [L, L, P, D, D, I, D, P, D, D, D, P, P, P]),
+                "orc_step_ssprk3_euler2d_ext": (I, [L, L, D, D, I, D, P, D, D, D, P, D]),
                 "orc_rhs_euler1d": (I, [L, P, D, I, I, D, P, P, P, P, P, P]),
                 "orc_rhs_euler2d": (I, [L, L, P, D, D, I, I, D, P, P, P, P, P, P, P]),
                 "orc_euler_eigen": (I, [I, D, P, P, P, P, P]),
@@ -215,6 +218,54 @@ def rhs_burgers(u, h, R, bc=BC_PERIODIC, forced=None, want_sel=False, want_win=F
     if want_count:
         out["ntested"] = cnt.value
     return out
+
+
+def side(kind_lo, state_lo=None, kind_hi=None, state_hi=None, split0=np.inf, rate=0.0):
+    """A boundary side: kind_lo below the along-side position split0 + rate t,
+    kind_hi above it (SIDE_TRANSMISSIVE, SIDE_REFLECTIVE, SIDE_INFLOW with a
+    conserved state (rho, rho u, rho v, E))."""
+    kind_hi = kind_lo if kind_hi is None else kind_hi
+    z = np.zeros(4)
+    return np.concatenate([[kind_lo, kind_hi, split0, rate],
+                           z if state_lo is None else np.asarray(state_lo, dtype=np.float64),
+                           z if state_hi is None else np.asarray(state_hi, dtype=np.float64)])
+
+
+def _sides(sides):
+    """[x low, x high, y low, y high] -> 48 doubles (None: transmissive)."""
+    t = side(SIDE_TRANSMISSIVE)
+    return np.ascontiguousarray(np.concatenate([t if s_ is None else s_ for s_ in sides]))
+
+
+def rhs_euler2d_ext(U, dx, dy, R, sides=(None, None, None, None), t=0.0, gravity=(0.0, 0.0),
+                    gamma=1.4, forced=None, want_sel=False):
+    """2D Euler on [0, nx dx] x [0, ny dy] with boundary sides at time t and a
+    body force (gx, gy): S = (0, rho gx, rho gy, rho u gx + rho v gy)."""
+    U = _f64(U)
+    _, ny, nx = U.shape
+    rhs = np.zeros_like(U)
+    nsel = 8 * ny * (nx + 1) + 8 * nx * (ny + 1)
+    sel = np.zeros(nsel, dtype=np.uint8) if want_sel else None
+    fz = None if forced is None else np.ascontiguousarray(forced, dtype=np.uint8)
+    sd = _sides(sides)
+    _check(_load().orc_rhs_euler2d_ext(nx, ny, _p(U), dx, dy, R, gamma, _p(sd), t, gravity[0],
+                                       gravity[1], _p(fz), _p(sel), _p(rhs)))
+    out = {"rhs": rhs}
+    if want_sel:
+        out["sel"] = sel
+    return out
+
+
+def step_euler2d_ext(U, dx, dy, R, dt, sides=(None, None, None, None), t=0.0,
+                     gravity=(0.0, 0.0), gamma=1.4):
+    """One SSP-RK3 step from time t (stage right-hand sides at t, t + dt,
+    t + dt/2)."""
+    U = _f64(U).copy()
+    _, ny, nx = U.shape
+    sd = _sides(sides)
+    _check(_load().orc_step_ssprk3_euler2d_ext(nx, ny, dx, dy, R, gamma, _p(sd), t, gravity[0],
+                                               gravity[1], _p(U), dt))
+    return U
 
 
 def rhs_euler1d(U, h, R, bc=BC_TRANSMISSIVE, gamma=1.4, forced=None, want_sel=False,

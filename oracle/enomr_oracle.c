@@ -624,6 +624,50 @@ static int line_alpha_frozen(int c, double gamma, const double *Ul, const int *a
     return ORC_OK;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Boundary sides (the 2D problems of Sec. 4.4).  A side is described by 12  */
+/* doubles: kind below and above a split position along the side, the split  */
+/* position s0 + rate * t, and a conserved state (rho, rho u, rho v, E) for   */
+/* each part.  Kinds: 1 transmissive (copy of the nearest cell), 2 reflective */
+/* (mirror image, normal momentum negated), 3 inflow (the given state).       */
+/* Along-side coordinate of a line: the cell centre of the row (x sides) or  */
+/* of the column (y sides), from the lower-left corner of the domain.        */
+/* ------------------------------------------------------------------------- */
+enum { SIDE_TRANSMISSIVE = 1, SIDE_REFLECTIVE = 2, SIDE_INFLOW = 3 };
+
+typedef struct {
+    const double *d; /* 12 doubles, or NULL: transmissive */
+    double pos, t;   /* along-side coordinate of the line, time */
+    int normal;      /* global component of the normal momentum (1: x, 2: y) */
+} side_t;
+
+/* Ghost cell j (< 0 or >= N) of a line of c components (line order rho,
+ * m_n, [m_t], E) into G. */
+static void side_ghost(const side_t *sd, int c, long j, long N, const double *Ul, double *G)
+{
+    int kind = SIDE_TRANSMISSIVE, q;
+    const double *st = NULL;
+    if (sd && sd->d) {
+        const int lo = sd->pos < sd->d[2] + sd->d[3] * sd->t;
+        kind = (int)(lo ? sd->d[0] : sd->d[1]);
+        st = sd->d + (lo ? 4 : 8);
+    }
+    if (kind == SIDE_REFLECTIVE) {
+        const long m = j < 0 ? -1 - j : 2 * N - 1 - j;
+        for (q = 0; q < c; ++q) G[q] = Ul[m * c + q];
+        G[1] = -G[1];
+    } else if (kind == SIDE_INFLOW) {
+        /* global (rho, m_x, m_y, E) -> line (rho, m_n, [m_t], E) */
+        G[0] = st[0];
+        G[1] = st[sd->normal];
+        if (c == 4) G[2] = st[sd->normal == 1 ? 2 : 1];
+        G[c - 1] = st[3];
+    } else {
+        const long m = j < 0 ? 0 : N - 1;
+        for (q = 0; q < c; ++q) G[q] = Ul[m * c + q];
+    }
+}
+
 /* One 1D sweep over a line of N cells (cell-major, Ul[i*c + comp]).
  * Writes the numerical fluxes fhat[(N+1)*c] at interfaces k = 0..N.
  * sel/win (optional) for this line: sel[side][field][N+1],
@@ -631,7 +675,8 @@ static int line_alpha_frozen(int c, double gamma, const double *Ul, const int *a
 static int sweep_line(int c, double gamma, const order_t *o, int bc, long N, const double *Ul,
                       const double *alpha_fixed, const int *amax_in, int *amax_out,
                       const uint8_t *forced, uint8_t *sel_out,
-                      double *win_out, double *fhat, double *alpha_out, long *ntested)
+                      double *win_out, double *fhat, double *alpha_out, long *ntested,
+                      const side_t *lo, const side_t *hi)
 {
     int g = o->g, st, q, k, l;
     long i, j;
@@ -651,7 +696,12 @@ static int sweep_line(int c, double gamma, const order_t *o, int bc, long N, con
     /* ghost fill and physical flux per cell */
     for (j = -g; j < N + g && !st; ++j) {
         prim_t P;
+        double Gs[4];
         const double *U = Ul + ghost_index(j, N, bc) * c;
+        if ((lo || hi) && (j < 0 || j >= N)) {
+            side_ghost(j < 0 ? lo : hi, c, j, N, Ul, Gs);
+            U = Gs;
+        }
         for (q = 0; q < c; ++q) Ug[(j + g) * c + q] = U[q];
         if (primitive(c, gamma, U, &P)) {
             st = ORC_ENONPHYS;
@@ -738,7 +788,7 @@ static int rhs_euler1d(long N, const double *U, double h, int R, int bc, double 
     for (i = 0; i < N; ++i)
         for (q = 0; q < 3; ++q) Ul[i * 3 + q] = U[q * N + i];
     st = sweep_line(3, gamma, o, bc, N, Ul, NULL, amax_in, amax_out, forced, sel_out, win_out,
-                    fhat, alpha_out, &ntested);
+                    fhat, alpha_out, &ntested, NULL, NULL);
     if (!st)
         for (i = 0; i < N; ++i)
             for (q = 0; q < 3; ++q) rhs[q * N + i] = -(fhat[(i + 1) * 3 + q] - fhat[i * 3 + q]) / h;
@@ -776,7 +826,8 @@ static int rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, 
                        double gamma, const double *afx, const double *afy,
                        const int *amx_in, const int *amy_in, int *amx_out,
                        int *amy_out, const uint8_t *forced, uint8_t *sel_out, double *win_out,
-                       double *rhs, double *alpha_x, double *alpha_y, long *ntested_out)
+                       double *rhs, double *alpha_x, double *alpha_y, long *ntested_out,
+                       const double *sides, double t, double gx, double gy)
 {
     const order_t *o = get_order(R);
     const long ncell = nx * ny;
@@ -807,10 +858,15 @@ static int rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, 
         if (forced)
             for (r = 0; r < 8; ++r)
                 memcpy(fl + r * (nx + 1), forced + ((long)r * ny + y) * (nx + 1), nx + 1);
-        lst = sweep_line(4, gamma, o, bc, nx, Ul, afx ? afx + y * 4 : NULL,
-                         amx_in ? amx_in + y * 4 : NULL,
-                         amx_out ? amx_out + y * 4 : NULL, fl, sl, wl, fh,
-                         alpha_x ? alpha_x + y * 4 : NULL, &nt);
+        {
+            const side_t slo = {sides, (y + 0.5) * dy, t, 1};
+            const side_t shi = {sides ? sides + 12 : NULL, (y + 0.5) * dy, t, 1};
+            lst = sweep_line(4, gamma, o, bc, nx, Ul, afx ? afx + y * 4 : NULL,
+                             amx_in ? amx_in + y * 4 : NULL,
+                             amx_out ? amx_out + y * 4 : NULL, fl, sl, wl, fh,
+                             alpha_x ? alpha_x + y * 4 : NULL, &nt, sides ? &slo : NULL,
+                             sides ? &shi : NULL);
+        }
         ntested += nt;
         if (lst) {
 #pragma omp critical
@@ -859,10 +915,15 @@ static int rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, 
         if (forced)
             for (r = 0; r < 8; ++r)
                 memcpy(fl + r * (ny + 1), forced + ysel_off + ((long)r * nx + x) * (ny + 1), ny + 1);
-        lst = sweep_line(4, gamma, o, bc, ny, Ul, afy ? afy + x * 4 : NULL,
-                         amy_in ? amy_in + x * 4 : NULL,
-                         amy_out ? amy_out + x * 4 : NULL, fl, sl, wl, fh,
-                         alpha_y ? alpha_y + x * 4 : NULL, &nt);
+        {
+            const side_t slo = {sides ? sides + 24 : NULL, (x + 0.5) * dx, t, 2};
+            const side_t shi = {sides ? sides + 36 : NULL, (x + 0.5) * dx, t, 2};
+            lst = sweep_line(4, gamma, o, bc, ny, Ul, afy ? afy + x * 4 : NULL,
+                             amy_in ? amy_in + x * 4 : NULL,
+                             amy_out ? amy_out + x * 4 : NULL, fl, sl, wl, fh,
+                             alpha_y ? alpha_y + x * 4 : NULL, &nt, sides ? &slo : NULL,
+                             sides ? &shi : NULL);
+        }
         ntested += nt;
         if (lst) {
 #pragma omp critical
@@ -879,6 +940,14 @@ static int rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, 
                 rhs[1 * ncell + idx] = xpart[1 * ncell + idx] + g1;
                 rhs[2 * ncell + idx] = xpart[2 * ncell + idx] + g2;
                 rhs[3 * ncell + idx] = xpart[3 * ncell + idx] + g3;
+                if (gx != 0.0 || gy != 0.0) {
+                    /* body force (gx, gy): S = (0, rho gx, rho gy, rho u gx + rho v gy) */
+                    const double rho = U[0 * ncell + idx], mx = U[1 * ncell + idx];
+                    const double my = U[2 * ncell + idx];
+                    rhs[1 * ncell + idx] = rhs[1 * ncell + idx] + rho * gx;
+                    rhs[2 * ncell + idx] = rhs[2 * ncell + idx] + rho * gy;
+                    rhs[3 * ncell + idx] = rhs[3 * ncell + idx] + (my * gy + mx * gx);
+                }
             }
             for (r = 0; r < 8; ++r) {
                 if (sel_out)
@@ -904,7 +973,18 @@ int orc_rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, int
                     double *rhs, double *alpha_x, double *alpha_y, long *ntested_out)
 {
     return rhs_euler2d(nx, ny, U, dx, dy, R, bc, gamma, NULL, NULL, NULL, NULL, NULL, NULL, forced,
-                       sel_out, win_out, rhs, alpha_x, alpha_y, ntested_out);
+                       sel_out, win_out, rhs, alpha_x, alpha_y, ntested_out, NULL, 0.0, 0.0, 0.0);
+}
+
+/* 2D Euler on [0, nx dx] x [0, ny dy] with boundary sides (4 x 12 doubles:
+ * x low, x high, y low, y high; see side_t) at time t and a body force
+ * (gx, gy).  bc must be transmissive; sel as orc_rhs_euler2d. */
+int orc_rhs_euler2d_ext(long nx, long ny, const double *U, double dx, double dy, int R,
+                        double gamma, const double *sides, double t, double gx, double gy,
+                        const uint8_t *forced, uint8_t *sel_out, double *rhs)
+{
+    return rhs_euler2d(nx, ny, U, dx, dy, R, 1, gamma, NULL, NULL, NULL, NULL, NULL, NULL, forced,
+                       sel_out, NULL, rhs, NULL, NULL, NULL, sides, t, gx, gy);
 }
 
 /* 2D Euler with every discrete choice given (stencils and, per row and per
@@ -916,7 +996,7 @@ int orc_rhs_euler2d_frozen(long nx, long ny, const double *U, double dx, double 
                            const int *amy_in, int *amx_out, int *amy_out, double *rhs)
 {
     return rhs_euler2d(nx, ny, U, dx, dy, R, bc, gamma, NULL, NULL, amx_in, amy_in, amx_out,
-                       amy_out, forced, NULL, NULL, rhs, NULL, NULL, NULL);
+                       amy_out, forced, NULL, NULL, rhs, NULL, NULL, NULL, NULL, 0.0, 0.0, 0.0);
 }
 
 /* 2D Euler with the stencils forced and the split speeds given as values
@@ -927,7 +1007,7 @@ int orc_rhs_euler2d_alpha(long nx, long ny, const double *U, double dx, double d
                           const double *alpha_y, double *rhs)
 {
     return rhs_euler2d(nx, ny, U, dx, dy, R, bc, gamma, alpha_x, alpha_y, NULL, NULL, NULL, NULL,
-                       forced, NULL, NULL, rhs, NULL, NULL, NULL);
+                       forced, NULL, NULL, rhs, NULL, NULL, NULL, NULL, 0.0, 0.0, 0.0);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1024,6 +1104,35 @@ int orc_step_ssprk3(int eq, long nx, long ny, double dx, double dy, int R, int b
     if (!st) {
         for (i = 0; i < n; ++i) U2[i] = 0.75 * U[i] + 0.25 * (U1[i] + dt * L[i]);
         st = prob_rhs(&P, U2, L);
+    }
+    if (!st)
+        for (i = 0; i < n; ++i) U[i] = (1.0 / 3.0) * U[i] + (2.0 / 3.0) * (U2[i] + dt * L[i]);
+    free(L);
+    free(U1);
+    free(U2);
+    return st;
+}
+
+/* Eq. (TVD3rdRK) for 2D Euler with boundary sides and a body force: the
+ * stage right-hand sides are taken at t, t + dt and t + dt/2. */
+int orc_step_ssprk3_euler2d_ext(long nx, long ny, double dx, double dy, int R, double gamma,
+                                const double *sides, double t, double gx, double gy, double *U,
+                                double dt)
+{
+    long n = 4 * nx * ny, i;
+    double *L = (double *)malloc(sizeof(double) * n);
+    double *U1 = (double *)malloc(sizeof(double) * n);
+    double *U2 = (double *)malloc(sizeof(double) * n);
+    int st = orc_rhs_euler2d_ext(nx, ny, U, dx, dy, R, gamma, sides, t, gx, gy, NULL, NULL, L);
+    if (!st) {
+        for (i = 0; i < n; ++i) U1[i] = U[i] + dt * L[i];
+        st = orc_rhs_euler2d_ext(nx, ny, U1, dx, dy, R, gamma, sides, t + dt, gx, gy, NULL, NULL,
+                                 L);
+    }
+    if (!st) {
+        for (i = 0; i < n; ++i) U2[i] = 0.75 * U[i] + 0.25 * (U1[i] + dt * L[i]);
+        st = orc_rhs_euler2d_ext(nx, ny, U2, dx, dy, R, gamma, sides, t + 0.5 * dt, gx, gy, NULL,
+                                 NULL, L);
     }
     if (!st)
         for (i = 0; i < n; ++i) U[i] = (1.0 / 3.0) * U[i] + (2.0 / 3.0) * (U2[i] + dt * L[i]);

@@ -149,18 +149,78 @@ def riemann2d(nx: int, ny: int | None = None, seed: int = 0, xc=0.8, yc=0.8, gam
     return conserved_2d(prim[..., 0], prim[..., 1], prim[..., 2], prim[..., 3], gamma), dx, dy
 
 
-def riemann2d_rp1(n: int, gamma=GAMMA):
-    """The paper's first 2D Riemann configuration on [-1,1]^2 (Sec. 4.4)."""
+def _quadrants(n: int, states, gamma=GAMMA):
+    """Four constant states on [-1,1]^2 split at x = 0 and y = 0 (cell
+    centres; keys 'll', 'lu', 'uu', 'ul' = (x side, y side))."""
     x, dx = centred_grid(-1.0, 1.0, n)
     X, Y = np.meshgrid(x, x)
-    st = {  # (rho, u, v, p)
-        "ll": (0.138, 1.206, 1.206, 0.029), "lu": (0.5323, 1.206, 0.0, 0.3),
-        "uu": (1.5, 0.0, 0.0, 1.5), "ul": (0.5323, 0.0, 1.206, 0.3)}
     out = np.zeros((4, n, n))
-    for key, (r, u, v, p) in st.items():
+    for key, (r, u, v, p) in states.items():
         m = ((X < 0) if key[0] == "l" else (X >= 0)) & ((Y < 0) if key[1] == "l" else (Y >= 0))
         out[:, m] = conserved_2d(np.array([r]), u, v, p, gamma)[:, 0][:, None]
     return out, dx, dx
+
+
+def riemann2d_rp1(n: int, gamma=GAMMA):
+    """The paper's first 2D Riemann configuration on [-1,1]^2 (Sec. 4.4):
+    four shocks; symmetric about the diagonal x = y (with u <-> v)."""
+    return _quadrants(n, {"ll": (0.138, 1.206, 1.206, 0.029), "lu": (0.5323, 1.206, 0.0, 0.3),
+                          "uu": (1.5, 0.0, 0.0, 1.5), "ul": (0.5323, 0.0, 1.206, 0.3)}, gamma)
+
+
+def riemann2d_rp2(n: int, gamma=GAMMA):
+    """The paper's second 2D Riemann configuration (Sec. 4.4): four contact
+    discontinuities."""
+    return _quadrants(n, {"ll": (1.0, -0.75, 0.5, 1.0), "lu": (2.0, 0.75, 0.5, 1.0),
+                          "uu": (1.0, 0.75, -0.5, 1.0), "ul": (3.0, -0.75, -0.5, 1.0)}, gamma)
+
+
+def double_mach(nx: int = 1200, ny: int = 300, gamma=GAMMA):
+    """Double Mach reflection (Sec. 4.4) on [0, 4] x [0, 1], cell centres: a
+    Mach 10 shock at 60 degrees through (1/6, 0).  Returns U, dx, dy and the
+    boundary sides (x low, x high, y low, y high) as tuples
+    (kind_lo, state_lo, kind_hi, state_hi, split0, rate) with kinds
+    'transmissive', 'reflective', 'inflow' and conserved states:
+    post-shock inflow on the left; transmissive on the right; at the
+    bottom transmissive for x < 1/6 and reflective beyond; at the top the
+    exact shock position 1/6 + (1 + 20 t)/sqrt(3) separates post- from
+    pre-shock inflow."""
+    x, dx = centred_grid(0.0, 4.0, nx)
+    y, dy = centred_grid(0.0, 1.0, ny)
+    X, Y = np.meshgrid(x, y)
+    s60, c60 = np.sin(np.pi / 3), np.cos(np.pi / 3)
+    post = conserved_2d(np.array([8.0]), 8.25 * s60, -8.25 * c60, 116.5, gamma)[:, 0]
+    pre = conserved_2d(np.array([1.4]), 0.0, 0.0, 1.0, gamma)[:, 0]
+    behind = X < 1.0 / 6.0 + Y / np.sqrt(3.0)
+    U = np.where(behind[None], post[:, None, None], pre[:, None, None])
+    sides = (("inflow", post, "inflow", post, np.inf, 0.0),
+             ("transmissive", None, "transmissive", None, np.inf, 0.0),
+             ("transmissive", None, "reflective", None, 1.0 / 6.0, 0.0),
+             ("inflow", post, "inflow", pre, 1.0 / 6.0 + 1.0 / np.sqrt(3.0), 20.0 / np.sqrt(3.0)))
+    return np.ascontiguousarray(U), dx, dy, sides
+
+
+def rayleigh_taylor(nx: int = 128, ny: int = 512, gamma=5.0 / 3.0):
+    """Rayleigh-Taylor instability (Sec. 4.4) on [0, 0.25] x [0, 1], gamma
+    5/3, body force (0, 1): heavy fluid (rho = 2) below y = 0.5, light
+    (rho = 1) above, p = 2y + 1 below and y + 1.5 above, v = -0.025 c
+    cos(8 pi x).  Sides: reflective left and right; inflow of the rest
+    states (2, 0, 0, 1) at the bottom and (1, 0, 0, 2.5) at the top."""
+    x, dx = centred_grid(0.0, 0.25, nx)
+    y, dy = centred_grid(0.0, 1.0, ny)
+    X, Y = np.meshgrid(x, y)
+    low = Y < 0.5
+    rho = np.where(low, 2.0, 1.0)
+    p = np.where(low, 2.0 * Y + 1.0, Y + 1.5)
+    v = -0.025 * np.sqrt(gamma * p / rho) * np.cos(8.0 * np.pi * X)
+    U = conserved_2d(rho, 0.0, v, p, gamma)
+    bottom = conserved_2d(np.array([2.0]), 0.0, 0.0, 1.0, gamma)[:, 0]
+    top = conserved_2d(np.array([1.0]), 0.0, 0.0, 2.5, gamma)[:, 0]
+    sides = (("reflective", None, "reflective", None, np.inf, 0.0),
+             ("reflective", None, "reflective", None, np.inf, 0.0),
+             ("inflow", bottom, "inflow", bottom, np.inf, 0.0),
+             ("inflow", top, "inflow", top, np.inf, 0.0))
+    return np.ascontiguousarray(U), dx, dy, sides
 
 
 def isentropic_vortex(n: int, strength=5.0, gamma=GAMMA, L=10.0, centre=None):
