@@ -145,6 +145,56 @@ ENOMR_API enomr_status enomr_step_lssp(enomr_ctx *ctx, double *U, double dt, int
 ENOMR_API enomr_status enomr_cfl_dt(enomr_ctx *ctx, const double *U, double cfl, double *dt_host);
 
 /*
+ * Boundary sides and body force of the 2D problems of Sec. 4.4 (double Mach
+ * reflection, Rayleigh-Taylor instability) for 2D Euler contexts created
+ * with ENOMR_TRANSMISSIVE.  The domain is [0, nx dx] x [0, ny dy]; a side's
+ * along-side coordinate of a line is the cell centre of the row (x sides)
+ * or column (y sides).  A side is split at position split0 + split_rate t
+ * (t the time of the stage; split0 = +inf: one kind everywhere): kind_lo
+ * applies below it, kind_hi above.  Kinds:
+ *   ENOMR_SIDE_TRANSMISSIVE  copy of the nearest cell (the default);
+ *   ENOMR_SIDE_REFLECTIVE    mirror image of the interior, normal momentum
+ *                            negated (needs at least g = (order+1)/2 cells
+ *                            across);
+ *   ENOMR_SIDE_INFLOW        the given conserved state (rho, rho u, rho v, E)
+ *                            in every ghost cell.
+ * Sides: 0 x low, 1 x high, 2 y low, 3 y high.  The adjoint entry points
+ * reject a context with sides set or a body force.
+ */
+typedef enum {
+    ENOMR_SIDE_TRANSMISSIVE = 1,
+    ENOMR_SIDE_REFLECTIVE = 2,
+    ENOMR_SIDE_INFLOW = 3
+} enomr_side_kind;
+
+typedef struct {
+    int kind_lo, kind_hi;
+    double split0, split_rate;
+    double state_lo[4], state_hi[4];
+} enomr_side;
+
+/* enomr_set_side -- set one side (copied; synchronous).  ENOMR_EINVAL for a
+ * context that is not 2D Euler with transmissive boundaries, a bad kind or
+ * side, a reflective side across fewer than g cells, or a non-physical
+ * inflow state. */
+ENOMR_API enomr_status enomr_set_side(enomr_ctx *ctx, int side, const enomr_side *desc);
+
+/* enomr_set_body_force -- add S = (0, rho gx, rho gy, rho u gx + rho v gy)
+ * to the right-hand side after the two directional flux differences
+ * (2D Euler only); (0, 0) removes it. */
+ENOMR_API enomr_status enomr_set_body_force(enomr_ctx *ctx, double gx, double gy);
+
+/* enomr_set_time / enomr_get_time -- the time of the state the next
+ * enomr_step starts from (device scalar, 0 after enomr_init), which only
+ * boundary sides depend on.  With sides or a body force set, enomr_step and
+ * enomr_step_lssp advance it by their dt; the SSP-RK3 stages see t,
+ * t + dt, t + dt/2; enomr_rhs and enomr_debug_selection see t; stage s of
+ * enomr_stage sees t + c_s dt (c = 0, 1, 1/2).  Both synchronise the
+ * stream. */
+ENOMR_API enomr_status enomr_set_time(enomr_ctx *ctx, double t);
+ENOMR_API enomr_status enomr_get_time(enomr_ctx *ctx, double *t);
+
+/*
  * enomr_debug_selection -- the stencil chosen at every interface, field and
  * side for state U (same arithmetic as enomr_rhs).  sel (device, uint8):
  *   advection  [2][nx+1]

@@ -72,7 +72,7 @@ def _load():
                 "orc_mr_indicators": (I, [I, P, P, P, P, P]),
                 "orc_rhs_advection": (I, [L, P, D, I, I, D, P, P, P, P, P]),
                 "orc_rhs_burgers": (I, [L, P, D, I, I, P, P, P, P, P]),
-                "orc_rhs_euler2d_ext": (I, [L, L, P, D, D, I, D, P, D, D, D, P, P, P]),
+                "orc_rhs_euler2d_ext": (I, [L, L, P, D, D, I, D, P, D, D, D, P, P, P, P]),
                 "orc_step_ssprk3_euler2d_ext": (I, [L, L, D, D, I, D, P, D, D, D, P, D]),
                 "orc_rhs_euler1d": (I, [L, P, D, I, I, D, P, P, P, P, P, P]),
                 "orc_rhs_euler2d": (I, [L, L, P, D, D, I, I, D, P, P, P, P, P, P, P]),
@@ -238,21 +238,27 @@ def _sides(sides):
 
 
 def rhs_euler2d_ext(U, dx, dy, R, sides=(None, None, None, None), t=0.0, gravity=(0.0, 0.0),
-                    gamma=1.4, forced=None, want_sel=False):
+                    gamma=1.4, forced=None, want_sel=False, want_win=False):
     """2D Euler on [0, nx dx] x [0, ny dy] with boundary sides at time t and a
-    body force (gx, gy): S = (0, rho gx, rho gy, rho u gx + rho v gy)."""
+    body force (gx, gy): S = (0, rho gx, rho gy, rho u gx + rho v gy).
+    sel / win layouts as rhs_euler2d (win: one row of 2g-1 values per
+    selection entry)."""
     U = _f64(U)
     _, ny, nx = U.shape
+    g = (R + 1) // 2
     rhs = np.zeros_like(U)
     nsel = 8 * ny * (nx + 1) + 8 * nx * (ny + 1)
     sel = np.zeros(nsel, dtype=np.uint8) if want_sel else None
+    win = np.zeros(nsel * (2 * g - 1)) if want_win else None
     fz = None if forced is None else np.ascontiguousarray(forced, dtype=np.uint8)
     sd = _sides(sides)
     _check(_load().orc_rhs_euler2d_ext(nx, ny, _p(U), dx, dy, R, gamma, _p(sd), t, gravity[0],
-                                       gravity[1], _p(fz), _p(sel), _p(rhs)))
+                                       gravity[1], _p(fz), _p(sel), _p(win), _p(rhs)))
     out = {"rhs": rhs}
     if want_sel:
         out["sel"] = sel
+    if want_win:
+        out["win"] = win.reshape(nsel, 2 * g - 1)
     return out
 
 

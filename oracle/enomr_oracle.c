@@ -981,10 +981,10 @@ int orc_rhs_euler2d(long nx, long ny, const double *U, double dx, double dy, int
  * (gx, gy).  bc must be transmissive; sel as orc_rhs_euler2d. */
 int orc_rhs_euler2d_ext(long nx, long ny, const double *U, double dx, double dy, int R,
                         double gamma, const double *sides, double t, double gx, double gy,
-                        const uint8_t *forced, uint8_t *sel_out, double *rhs)
+                        const uint8_t *forced, uint8_t *sel_out, double *win_out, double *rhs)
 {
     return rhs_euler2d(nx, ny, U, dx, dy, R, 1, gamma, NULL, NULL, NULL, NULL, NULL, NULL, forced,
-                       sel_out, NULL, rhs, NULL, NULL, NULL, sides, t, gx, gy);
+                       sel_out, win_out, rhs, NULL, NULL, NULL, sides, t, gx, gy);
 }
 
 /* 2D Euler with every discrete choice given (stencils and, per row and per
@@ -1123,16 +1123,16 @@ int orc_step_ssprk3_euler2d_ext(long nx, long ny, double dx, double dy, int R, d
     double *L = (double *)malloc(sizeof(double) * n);
     double *U1 = (double *)malloc(sizeof(double) * n);
     double *U2 = (double *)malloc(sizeof(double) * n);
-    int st = orc_rhs_euler2d_ext(nx, ny, U, dx, dy, R, gamma, sides, t, gx, gy, NULL, NULL, L);
+    int st = orc_rhs_euler2d_ext(nx, ny, U, dx, dy, R, gamma, sides, t, gx, gy, NULL, NULL, NULL, L);
     if (!st) {
         for (i = 0; i < n; ++i) U1[i] = U[i] + dt * L[i];
         st = orc_rhs_euler2d_ext(nx, ny, U1, dx, dy, R, gamma, sides, t + dt, gx, gy, NULL, NULL,
-                                 L);
+                                 NULL, L);
     }
     if (!st) {
         for (i = 0; i < n; ++i) U2[i] = 0.75 * U[i] + 0.25 * (U1[i] + dt * L[i]);
         st = orc_rhs_euler2d_ext(nx, ny, U2, dx, dy, R, gamma, sides, t + 0.5 * dt, gx, gy, NULL,
-                                 NULL, L);
+                                 NULL, NULL, L);
     }
     if (!st)
         for (i = 0; i < n; ++i) U[i] = (1.0 / 3.0) * U[i] + (2.0 / 3.0) * (U2[i] + dt * L[i]);

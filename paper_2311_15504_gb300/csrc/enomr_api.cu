@@ -37,6 +37,11 @@ struct enomr_ctx {
     // optional per-kernel event timing (enomr_profile_begin/end)
     int prof_kernel, prof_max, prof_n;
     cudaEvent_t *prof_ev;
+    // boundary sides (x low, x high, y low, y high), body force, time
+    SideDev *sides_d;
+    bool custom_sides;
+    double gx, gy;
+    double *t_dev;
 };
 
 static void prof_start(enomr_ctx *c, int k)
@@ -212,8 +217,19 @@ __global__ void k_axpy(long long n, double a, const double *x, double *y, int ac
 
 __global__ void k_set_dt(const double *smax, double cfl, double dt_fixed, double *dt)
 {
-    // a state without any wave speed (Burgers with u = 0) is steady: dt = 0
-    *dt = dt_fixed > 0.0 ? dt_fixed : (*smax > 0.0 ? cfl / *smax : 0.0);
+    // a state without any wave speed (Burgers with u = 0) is steady: dt = 0;
+    // a non-finite maximum (a non-physical state, flagged in the status
+    // word) gives NaN, never a step that does not advance
+    const double sm = *smax;
+    *dt = dt_fixed > 0.0 ? dt_fixed
+                         : ((sm > 0.0 && sm < __longlong_as_double(0x7ff0000000000000LL))
+                                ? cfl / sm
+                                : (sm == 0.0 ? 0.0 : __longlong_as_double(0x7ff8000000000000LL)));
+}
+
+__global__ void k_advance_time(double *t, const double *dt, double mult)
+{
+    *t = *t + mult * *dt;
 }
 
 // Burgers: max |u| over the line (the Lax-Friedrichs alpha and the CFL
@@ -305,6 +321,12 @@ template <int R> struct E1F {
 template <int R> struct E2XF {
     static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler2d_x<R>(a, s); }
 };
+template <int R> struct E2XEF {
+    static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler2d_x_ext<R>(a, s); }
+};
+template <int R> struct E2YEF {
+    static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler2d_y_ext<R>(a, s); }
+};
 template <int R> struct E2YF {
     static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler2d_y<R>(a, s); }
 };
@@ -384,12 +406,28 @@ static SweepArgs sweep_args(enomr_ctx *c, const double *U, bool ysweep)
     a.ft_out = nullptr;
     a.status = c->status;
     memset(&a.epi, 0, sizeof(a.epi));
+    a.side_lo = c->sides_d + (ysweep ? 2 : 0);
+    a.side_hi = c->sides_d + (ysweep ? 3 : 1);
+    a.pos_h = ysweep ? c->dx : c->dy;
+    a.t_dev = c->t_dev;
+    a.dt_time = c->dt;
+    a.t_coef = 0.0;
+    // the body force is added by the sweep that finishes the right-hand side
+    a.src = (c->gx != 0.0 || c->gy != 0.0) && ysweep;
+    a.g_n = ysweep ? c->gy : c->gx;
+    a.g_t = ysweep ? c->gx : c->gy;
     return a;
+}
+
+// boundary sides or a body force: the 2D sweeps' EXT instances
+static bool extended(const enomr_ctx *c)
+{
+    return c->custom_sides || c->gx != 0.0 || c->gy != 0.0;
 }
 
 // Evaluate L(U) into the epilogue.  The alpha of U must be current.
 static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilogue &epi,
-                                      uint8_t *sel, double *ft = nullptr)
+                                      uint8_t *sel, double *ft = nullptr, double t_coef = 0.0)
 {
     if (c->eq == ENOMR_ADVECTION || c->eq == ENOMR_BURGERS) {
         AdvArgs a;
@@ -423,8 +461,11 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     ax.ft_out = ft;
     ax.epi.mode = EPI_STORE;
     ax.epi.out = c->D;
+    ax.t_coef = t_coef;
+    const bool ext = extended(c);
     prof_start(c, 1);
-    cudaError_t e = by_order<E2XF>(c->order, ax, c->stream);
+    cudaError_t e = ext ? by_order<E2XEF>(c->order, ax, c->stream)
+                        : by_order<E2XF>(c->order, ax, c->stream);
     prof_stop(c, 1);
     CU_TRY(e);
     SweepArgs ay = sweep_args(c, U, true);
@@ -432,8 +473,9 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     ay.ft_out = ft ? ft + 4LL * c->ny * (c->nx + 1) : nullptr;
     ay.epi = epi;
     ay.epi.Dprev = c->D;
+    ay.t_coef = t_coef;
     prof_start(c, 2);
-    e = by_order<E2YF>(c->order, ay, c->stream);
+    e = ext ? by_order<E2YEF>(c->order, ay, c->stream) : by_order<E2YF>(c->order, ay, c->stream);
     prof_stop(c, 2);
     return cu(e);
 }
@@ -479,6 +521,8 @@ ENOMR_API void enomr_free(enomr_ctx *c)
     cudaFree(c->ayb);
     cudaFree(c->Ub1);
     cudaFree(c->Ub2);
+    cudaFree(c->sides_d);
+    cudaFree(c->t_dev);
     for (int i = 0; i < 2; ++i) {
         cudaFree(c->fsel[i]);
         cudaFree(c->fft[i]);
@@ -540,7 +584,9 @@ ENOMR_API enomr_status enomr_init(enomr_ctx **out, int eq, int ndim, int64_t nx,
               cudaMalloc(&c->axb, sizeof(double) * 3 * ny) == cudaSuccess &&
               cudaMalloc(&c->ayb, sizeof(double) * 3 * nx) == cudaSuccess &&
               cudaMalloc(&c->Ub1, sizeof(double) * c->nstate) == cudaSuccess &&
-              cudaMalloc(&c->Ub2, sizeof(double) * c->nstate) == cudaSuccess;
+              cudaMalloc(&c->Ub2, sizeof(double) * c->nstate) == cudaSuccess &&
+              cudaMalloc(&c->sides_d, sizeof(SideDev) * 4) == cudaSuccess &&
+              cudaMalloc(&c->t_dev, sizeof(double)) == cudaSuccess;
     if (ok && eq == ENOMR_EULER) {
         c->nsel = ndim == 2 ? 8 * ny * (nx + 1) + 8 * nx * (ny + 1) : 6 * (nx + 1);
         c->nft = ndim == 2 ? 4 * ny * (nx + 1) + 4 * nx * (ny + 1) : 3 * (nx + 1);
@@ -553,7 +599,9 @@ ENOMR_API enomr_status enomr_init(enomr_ctx **out, int eq, int ndim, int64_t nx,
         enomr_free(c);
         return ENOMR_ENOMEM;
     }
-    if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) {
+    if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->t_dev, 0, sizeof(double)) != cudaSuccess ||
+        cudaMemset(c->dt, 0, sizeof(double)) != cudaSuccess) {
         enomr_free(c);
         return ENOMR_ECUDA;
     }
@@ -597,7 +645,8 @@ static enomr_status stage_impl(enomr_ctx *c, int s, const double *Un, const doub
     e.dt_dev = c->dt;
     e.Un = Un;
     e.out = Uout;
-    return rhs_with_epilogue(c, Us, e, sel, ft);
+    static const double RK_T[3] = {0.0, 1.0, 0.5};  // stage times t + RK_T dt
+    return rhs_with_epilogue(c, Us, e, sel, ft, RK_T[s - 1]);
 }
 
 ENOMR_API enomr_status enomr_stage(enomr_ctx *c, int s, const double *Un, const double *Us,
@@ -634,6 +683,10 @@ ENOMR_API enomr_status enomr_step(enomr_ctx *c, double *U, double dt, double cfl
     if ((st = stage_impl(c, 1, U, U, c->U1, alpha_done))) return st;
     if ((st = stage_impl(c, 2, U, c->U1, c->U2))) return st;
     if ((st = stage_impl(c, 3, U, c->U2, U))) return st;
+    if (extended(c)) {  // the time only matters to boundary sides
+        k_advance_time<<<1, 1, 0, c->stream>>>(c->t_dev, c->dt, 1.0);
+        CU_TRY(cudaGetLastError());
+    }
     if (dt_used) {
         CU_TRY(cudaMemcpyAsync(dt_used, c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         CU_TRY(cudaStreamSynchronize(c->stream));
@@ -685,7 +738,8 @@ ENOMR_API enomr_status enomr_step_lssp(enomr_ctx *c, double *U, double dt, int m
         e.dt_dev = c->dt;
         e.Un = cur;
         e.out = next;
-        if ((st = rhs_with_epilogue(c, cur, e, nullptr))) return st;
+        // c->dt holds dt/2 here: stage s starts at t + (s - 1) dt/2
+        if ((st = rhs_with_epilogue(c, cur, e, nullptr, nullptr, (double)(s - 1)))) return st;
         if (s <= m - 2 && al[s] != 0.0)
             if ((st = axpy(c, al[s], next, acc, 1))) return st;
         cur = next;
@@ -701,7 +755,12 @@ ENOMR_API enomr_status enomr_step_lssp(enomr_ctx *c, double *U, double dt, int m
     e.dt_dev = c->dt;
     e.Un = acc;
     e.out = U;
-    return rhs_with_epilogue(c, cur, e, nullptr);
+    if ((st = rhs_with_epilogue(c, cur, e, nullptr, nullptr, (double)(m - 1)))) return st;
+    if (extended(c)) {  // t += dt (2 x the stored dt/2, exact)
+        k_advance_time<<<1, 1, 0, c->stream>>>(c->t_dev, c->dt, 2.0);
+        CU_TRY(cudaGetLastError());
+    }
+    return ENOMR_OK;
 }
 
 ENOMR_API enomr_status enomr_cfl_dt(enomr_ctx *c, const double *U, double cfl, double *dt_host)
@@ -823,7 +882,7 @@ ENOMR_API enomr_status enomr_rhs_vjp(enomr_ctx *c, const double *U, const double
 {
     if (!c || !U || !Lbar || !Ubar || (const double *)Ubar == U || (const double *)Ubar == Lbar)
         return ENOMR_EINVAL;
-    if (c->eq == ENOMR_BURGERS) return ENOMR_EINVAL;
+    if (c->eq == ENOMR_BURGERS || extended(c)) return ENOMR_EINVAL;
     if (!accumulate) CU_TRY(cudaMemsetAsync(Ubar, 0, sizeof(double) * c->nstate, c->stream));
     return rhs_vjp_impl(c, U, Lbar, Ubar, scale);
 }
@@ -832,7 +891,7 @@ ENOMR_API enomr_status enomr_step_vjp(enomr_ctx *c, const double *Un, double dt,
                                       const double *Ubar_np1, double *Ubar_n)
 {
     if (!c || !Un || !Ubar_np1 || !Ubar_n || !(dt > 0.0)) return ENOMR_EINVAL;
-    if (c->eq == ENOMR_BURGERS) return ENOMR_EINVAL;
+    if (c->eq == ENOMR_BURGERS || extended(c)) return ENOMR_EINVAL;
     if ((const double *)Ubar_n == Ubar_np1 || (const double *)Ubar_n == Un) return ENOMR_EINVAL;
     enomr_status st;
     // recompute the stages from the step's checkpoint U^n
@@ -878,6 +937,82 @@ ENOMR_API enomr_status enomr_debug_alpha(enomr_ctx *c, double *alpha_x, double *
         CU_TRY(cudaMemcpyAsync(alpha_bar_x, c->axb, bx, cudaMemcpyDeviceToDevice, c->stream));
     if (alpha_bar_y && c->ndim == 2)
         CU_TRY(cudaMemcpyAsync(alpha_bar_y, c->ayb, by, cudaMemcpyDeviceToDevice, c->stream));
+    return ENOMR_OK;
+}
+
+ENOMR_API enomr_status enomr_set_side(enomr_ctx *c, int side, const enomr_side *d)
+{
+    if (!c || !d || c->eq != ENOMR_EULER || c->ndim != 2 || c->bc != ENOMR_TRANSMISSIVE)
+        return ENOMR_EINVAL;
+    if (side < 0 || side > 3) return ENOMR_EINVAL;
+    const int g = (c->order + 1) / 2;
+    const long long across = side < 2 ? c->nx : c->ny;
+    const int kinds[2] = {d->kind_lo, d->kind_hi};
+    for (int i = 0; i < 2; ++i) {
+        if (kinds[i] < ENOMR_SIDE_TRANSMISSIVE || kinds[i] > ENOMR_SIDE_INFLOW) return ENOMR_EINVAL;
+        if (kinds[i] == ENOMR_SIDE_REFLECTIVE && across < g) return ENOMR_EINVAL;
+        const double *st = i ? d->state_hi : d->state_lo;
+        if (kinds[i] == ENOMR_SIDE_INFLOW) {
+            const double q2 = st[1] * st[1] + st[2] * st[2];
+            if (!(st[0] > 0.0) || !((st[3] - 0.5 * q2 / st[0]) > 0.0)) return ENOMR_EINVAL;
+        }
+    }
+    if (d->split0 != d->split0 || d->split_rate != d->split_rate) return ENOMR_EINVAL;
+    SideDev h[4];
+    if (c->custom_sides) {
+        CU_TRY(cudaMemcpy(h, c->sides_d, sizeof(h), cudaMemcpyDeviceToHost));
+    } else {
+        for (int i = 0; i < 4; ++i) {
+            memset(&h[i], 0, sizeof(SideDev));
+            h[i].kind_lo = h[i].kind_hi = SIDE_TRANSMISSIVE;
+            h[i].split0 = __builtin_inf();
+        }
+    }
+    h[side].kind_lo = d->kind_lo;
+    h[side].kind_hi = d->kind_hi;
+    h[side].split0 = d->split0;
+    h[side].rate = d->split_rate;
+    for (int q = 0; q < 4; ++q) {
+        h[side].st_lo[q] = d->state_lo[q];
+        h[side].st_hi[q] = d->state_hi[q];
+    }
+    CU_TRY(cudaMemcpy(c->sides_d, h, sizeof(h), cudaMemcpyHostToDevice));
+    c->custom_sides = true;
+    return ENOMR_OK;
+}
+
+ENOMR_API enomr_status enomr_set_body_force(enomr_ctx *c, double gx, double gy)
+{
+    if (!c || c->eq != ENOMR_EULER || c->ndim != 2) return ENOMR_EINVAL;
+    if (gx != gx || gy != gy) return ENOMR_EINVAL;
+    if ((gx != 0.0 || gy != 0.0) && !c->custom_sides) {
+        // the EXT sweeps read the sides: make them the default ones
+        SideDev h[4];
+        for (int i = 0; i < 4; ++i) {
+            memset(&h[i], 0, sizeof(SideDev));
+            h[i].kind_lo = h[i].kind_hi = SIDE_TRANSMISSIVE;
+            h[i].split0 = __builtin_inf();
+        }
+        CU_TRY(cudaMemcpy(c->sides_d, h, sizeof(h), cudaMemcpyHostToDevice));
+    }
+    c->gx = gx;
+    c->gy = gy;
+    return ENOMR_OK;
+}
+
+ENOMR_API enomr_status enomr_set_time(enomr_ctx *c, double t)
+{
+    if (!c || t != t) return ENOMR_EINVAL;
+    CU_TRY(cudaMemcpyAsync(c->t_dev, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));
+    return ENOMR_OK;
+}
+
+ENOMR_API enomr_status enomr_get_time(enomr_ctx *c, double *t)
+{
+    if (!c || !t) return ENOMR_EINVAL;
+    CU_TRY(cudaMemcpyAsync(t, c->t_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU_TRY(cudaStreamSynchronize(c->stream));
     return ENOMR_OK;
 }
 

@@ -40,7 +40,9 @@ __device__ __forceinline__ CellWaves cell_waves(double rho, double mx, double my
     const double ir = 1.0 / rho;  // IEEE division: never contracted
     const double u = __dmul_rn(mx, ir);
     const double v = (C == 4) ? __dmul_rn(my, ir) : 0.0;
-    const double ke = (C == 4) ? __fma_rn(u, u, __dmul_rn(v, v)) : __dmul_rn(u, u);
+    // u^2 + v^2 in a form symmetric in u and v, so that a state symmetric
+    // under x <-> y (with u <-> v) has bitwise equal x- and y-line speeds
+    const double ke = (C == 4) ? __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)) : __dmul_rn(u, u);
     const double p = __dmul_rn(gm1, __fma_rn(-0.5 * rho, ke, E));
     if (!positive(rho) || !positive(p) || !below_1e300(E)) atomicOr(status, ST_NONPHYS_CELL);
     const double c2 = __dmul_rn(__dmul_rn(gamma, p), ir);

@@ -28,6 +28,16 @@ struct Epilogue {
     double *out;
 };
 
+// A boundary side (device copy of enomr_side): kind below / above the
+// along-side position split0 + rate t, with an inflow state each
+// (conserved, global component order rho, m_x, m_y, E).
+enum : int { SIDE_TRANSMISSIVE = 1, SIDE_REFLECTIVE = 2, SIDE_INFLOW = 3 };
+struct SideDev {
+    int kind_lo, kind_hi;
+    double split0, rate;
+    double st_lo[4], st_hi[4];
+};
+
 // One 1D line sweep of the Euler equations (1D: C = 3; 2D x or y sweep: C = 4).
 struct SweepArgs {
     const double *U;       // stage state, [C][ny][nx]
@@ -41,6 +51,16 @@ struct SweepArgs {
     double *ft_out;        // optional: f^+ + f^- per field and interface, [C][lines][nlen+1]
     int *status;
     Epilogue epi;
+    // 2D sweeps with boundary sides or a body force (the EXT instances):
+    // sides at the low / high end of the lines
+    const SideDev *side_lo, *side_hi;
+    double pos_h;          // along-side coordinate of line L: (L + 1/2) pos_h
+    const double *t_dev;   // time of U^n; the stage is at *t_dev + t_coef * *dt_time
+    const double *dt_time;
+    double t_coef;
+    // body force in line components (normal, tangential); applied when src
+    int src;
+    double g_n, g_t;
 };
 
 struct AdvArgs {
@@ -107,6 +127,8 @@ template <int R> cudaError_t launch_advection(const AdvArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_burgers(const AdvArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler1d(const SweepArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, cudaStream_t s);
+template <int R> cudaError_t launch_euler2d_x_ext(const SweepArgs &a, cudaStream_t s);
+template <int R> cudaError_t launch_euler2d_y_ext(const SweepArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, cudaStream_t s);
 
 // Transpose-Jacobian product of one sweep (enomr_vjp.cuh).

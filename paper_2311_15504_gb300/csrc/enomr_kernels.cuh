@@ -132,9 +132,11 @@ __device__ __forceinline__ void load_a_table(double *sA, int tid, int nthreads)
 // ---------------------------------------------------------------------------
 // Epilogue: D -> output
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double epilogue(const Epilogue &e, long long idx, double D, double Us)
+__device__ __forceinline__ double epilogue(const Epilogue &e, long long idx, double D, double Us,
+                                          bool src = false, double S = 0.0)
 {
     if (e.Dprev) D = e.Dprev[idx] + D;
+    if (src) D = D + S;  // body force, after the two directional differences
     double o;
     if (e.mode == EPI_STORE) {
         o = D;

@@ -52,8 +52,27 @@ template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, cudaStream_t s
 template cudaError_t launch_advection<ENOMR_R>(const AdvArgs &, cudaStream_t);
 template cudaError_t launch_burgers<ENOMR_R>(const AdvArgs &, cudaStream_t);
 template cudaError_t launch_euler1d<ENOMR_R>(const SweepArgs &, cudaStream_t);
+// with boundary sides / body force (the 2D problems of Sec. 4.4)
+template <int R> cudaError_t launch_euler2d_x_ext(const SweepArgs &a, cudaStream_t s)
+{
+    const long long tx = (a.nx + X_TP - 2) / (X_TP - 1);
+    const long long ty = (a.ny + X_NL - 1) / X_NL;
+    k_sweep<R, 4, 0, X_TP, X_NL, true><<<dim3((unsigned)tx, (unsigned)ty), X_TP * X_NL, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t launch_euler2d_y_ext(const SweepArgs &a, cudaStream_t s)
+{
+    const long long tx = (a.nx + Y_NL - 1) / Y_NL;
+    const long long ty = (a.ny + Y_TP - 2) / (Y_TP - 1);
+    k_sweep<R, 4, 1, Y_TP, Y_NL, true><<<dim3((unsigned)tx, (unsigned)ty), Y_TP * Y_NL, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_euler2d_x<ENOMR_R>(const SweepArgs &, cudaStream_t);
 template cudaError_t launch_euler2d_y<ENOMR_R>(const SweepArgs &, cudaStream_t);
+template cudaError_t launch_euler2d_x_ext<ENOMR_R>(const SweepArgs &, cudaStream_t);
+template cudaError_t launch_euler2d_y_ext<ENOMR_R>(const SweepArgs &, cudaStream_t);
 
 }  // namespace enomr
 

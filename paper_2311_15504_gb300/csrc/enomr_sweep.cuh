@@ -41,6 +41,46 @@ struct SweepSmem {
     int nlist;
 };
 
+// State of ghost cell craw (< 0 or >= the line length) of line L, in
+// global component order, for a sweep with boundary sides: the kind of its
+// side at the line's along-side position gives a copy of the nearest cell,
+// the mirror image with the normal momentum negated, or the inflow state.
+template <int C, int DIR>
+__device__ __forceinline__ void side_cell(const SweepArgs &A, long long craw, long long L,
+                                          double *u)
+{
+    constexpr int QN = (DIR == 0) ? 1 : 2;
+    const long long nx = A.nx, ny = A.ny, ncell = nx * ny;
+    const long long nlen = (DIR == 0) ? nx : ny;
+    const SideDev &sd = craw < 0 ? *A.side_lo : *A.side_hi;
+    // stage time; dt is not read when the stage sits at t (a lone RHS
+    // evaluation may come before any step has set it)
+    const double ts =
+        A.t_coef != 0.0 ? __dadd_rn(*A.t_dev, __dmul_rn(A.t_coef, *A.dt_time)) : *A.t_dev;
+    const double pos = __dmul_rn(__dadd_rn((double)L, 0.5), A.pos_h);
+    const bool lo = pos < __dadd_rn(sd.split0, __dmul_rn(sd.rate, ts));
+    const int kind = lo ? sd.kind_lo : sd.kind_hi;
+    if (kind == SIDE_INFLOW) {
+        const double *st = lo ? sd.st_lo : sd.st_hi;
+#pragma unroll
+        for (int q = 0; q < C; ++q) u[q] = st[q];
+        return;
+    }
+    long long cell;
+    if (kind == SIDE_REFLECTIVE) {
+        // mirror image; a tile may stage cells further out than any window
+        // reaches (lines shorter than the tile), which are kept in the line
+        cell = craw < 0 ? -1 - craw : 2 * nlen - 1 - craw;
+        cell = cell < 0 ? 0 : (cell >= nlen ? nlen - 1 : cell);
+    } else {
+        cell = craw < 0 ? 0 : nlen - 1;
+    }
+    const long long gi = (DIR == 0) ? L * nx + cell : cell * nx + L;
+#pragma unroll
+    for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
+    if (kind == SIDE_REFLECTIVE) u[QN] = -u[QN];
+}
+
 // Flux of interface x_{k-1/2}, k = x0 + p, of tile line `line` into
 // sm.sFh[.][line][p] (and the selections / field values when requested).
 // FLATP: the interface is flat (both sides' centre triples of cell states
@@ -200,7 +240,9 @@ __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0,
 
 // One tile: NL lines x TP interfaces starting at interface x0 of line l0.
 // All threads of the CTA must call it; it ends after its epilogue.
-template <int R, int C, int DIR, int TP, int NL>
+// EXT: the 2D sweep with boundary sides and a body force (SweepArgs'
+// side_lo, side_hi, ..., src set); the plain instances leave them unread.
+template <int R, int C, int DIR, int TP, int NL, bool EXT = false>
 __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, long long l0,
                                            const double *sA, SweepSmem<R, C, TP, NL> &sm)
 {
@@ -231,11 +273,16 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
         }
         long long L = l0 + line;
         if (L >= nlines) L = nlines - 1;
-        const long long cell = ghost(x0 - g + s, nlen, A.bc);
-        const long long gi = (DIR == 0) ? L * nx + cell : cell * nx + L;
         double u[C];
+        const long long craw = x0 - g + s;
+        if (EXT && (craw < 0 || craw >= nlen)) {
+            side_cell<C, DIR>(A, craw, L, u);
+        } else {
+            const long long cell = ghost(craw, nlen, A.bc);
+            const long long gi = (DIR == 0) ? L * nx + cell : cell * nx + L;
 #pragma unroll
-        for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
+            for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
+        }
         const StagedCell<C> sc_ = stage_cell<C>(u[0], u[QN], (C == 4) ? u[QT] : 0.0, u[C - 1], A.gm1);
         if (!positive(u[0]) || !positive(sc_.p) || !below_1e300(u[C - 1]))
             atomicOr(A.status, ST_NONPHYS_CELL);
@@ -326,7 +373,20 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
                 // map line component back to the state component
                 const int qs = (q == 1) ? QN : ((C == 4 && q == 2) ? QT : q);
                 const double D = -(sFh[q][line][p + 1] - sFh[q][line][p]) * A.inv_h;
-                o[q] = epilogue(A.epi, qs * ncell + gi, D, sU[q][line][sc]);
+                if constexpr (EXT) {
+                    // body force (0, rho g_n, rho g_t, m_n g_n + m_t g_t)
+                    double S = 0.0;
+                    const double rho = sU[0][line][sc];
+                    if (q == 1) S = __dmul_rn(rho, A.g_n);
+                    if (C == 4 && q == 2) S = __dmul_rn(rho, A.g_t);
+                    if (q == C - 1)
+                        S = (C == 4) ? __dadd_rn(__dmul_rn(sU[1][line][sc], A.g_n),
+                                                 __dmul_rn(sU[2][line][sc], A.g_t))
+                                     : __dmul_rn(sU[1][line][sc], A.g_n);
+                    o[q] = epilogue(A.epi, qs * ncell + gi, D, sU[q][line][sc], A.src != 0, S);
+                } else {
+                    o[q] = epilogue(A.epi, qs * ncell + gi, D, sU[q][line][sc]);
+                }
             }
             if (C == 3 && A.alpha_next) {
                 double w3[3];
@@ -357,7 +417,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
     }
 }
 
-template <int R, int C, int DIR, int TP, int NL>
+template <int R, int C, int DIR, int TP, int NL, bool EXT = false>
 __global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
 {
     constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
@@ -366,7 +426,7 @@ __global__ void __launch_bounds__(TP *NL, 2) k_sweep(SweepArgs A)
     load_a_table<R>(sA, threadIdx.x, TP * NL);
     const long long x0 = (long long)((DIR == 0) ? blockIdx.x : blockIdx.y) * (TP - 1);
     const long long l0 = (long long)((DIR == 0) ? blockIdx.y : blockIdx.x) * NL;
-    sweep_tile<R, C, DIR, TP, NL>(A, x0, l0, sA, sm);
+    sweep_tile<R, C, DIR, TP, NL, EXT>(A, x0, l0, sA, sm);
 }
 
 // ---------------------------------------------------------------------------

@@ -15,6 +15,15 @@ import os
 import torch
 
 ADVECTION, EULER, BURGERS = 0, 1, 2
+SIDE_TRANSMISSIVE, SIDE_REFLECTIVE, SIDE_INFLOW = 1, 2, 3
+_SIDE_KINDS = {"transmissive": SIDE_TRANSMISSIVE, "reflective": SIDE_REFLECTIVE,
+               "inflow": SIDE_INFLOW}
+
+
+class _Side(ctypes.Structure):
+    _fields_ = [("kind_lo", ctypes.c_int), ("kind_hi", ctypes.c_int),
+                ("split0", ctypes.c_double), ("split_rate", ctypes.c_double),
+                ("state_lo", ctypes.c_double * 4), ("state_hi", ctypes.c_double * 4)]
 PERIODIC, TRANSMISSIVE = 0, 1
 ORDERS = (5, 7, 9, 11, 13, 15, 17)
 
@@ -55,6 +64,10 @@ _SIGS = {
     "enomr_batch_step": (_I, [_P, _P, _D]),
     "enomr_batch_autotune": (_I, [_P, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "enomr_batch_get_status": (_I, [_P]),
+    "enomr_set_side": (_I, [_P, _I, _P]),
+    "enomr_set_body_force": (_I, [_P, _D, _D]),
+    "enomr_set_time": (_I, [_P, _D]),
+    "enomr_get_time": (_I, [_P, ctypes.POINTER(_D)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -232,6 +245,40 @@ class Solver:
         _check(_lib.enomr_profile_end(self._ctx, ctypes.byref(n), ctypes.byref(ms)),
                "enomr_profile_end")
         return n.value, ms.value
+
+    def set_side(self, side, kind_lo, state_lo=None, kind_hi=None, state_hi=None,
+                 split0=float("inf"), rate=0.0):
+        """Boundary side (0 x low, 1 x high, 2 y low, 3 y high): kind_lo below
+        the along-side position split0 + rate t, kind_hi above; kinds
+        'transmissive', 'reflective', 'inflow' (with a conserved state)."""
+        k_lo = _SIDE_KINDS.get(kind_lo, kind_lo)
+        k_hi = k_lo if kind_hi is None else _SIDE_KINDS.get(kind_hi, kind_hi)
+        d = _Side(k_lo, k_hi, float(split0), float(rate))
+        for q in range(4):
+            d.state_lo[q] = 0.0 if state_lo is None else float(state_lo[q])
+            d.state_hi[q] = 0.0 if state_hi is None else float(state_hi[q])
+        _check(_lib.enomr_set_side(self._ctx, int(side), ctypes.byref(d)), "enomr_set_side")
+
+    def set_sides(self, sides):
+        """Four sides as (kind_lo, state_lo, kind_hi, state_hi, split0, rate)."""
+        for i, sd in enumerate(sides):
+            self.set_side(i, sd[0], sd[1], sd[2], sd[3], sd[4], sd[5])
+
+    def set_body_force(self, gx, gy):
+        _check(_lib.enomr_set_body_force(self._ctx, float(gx), float(gy)),
+               "enomr_set_body_force")
+
+    @property
+    def time(self):
+        self._stream()
+        t = _D()
+        _check(_lib.enomr_get_time(self._ctx, ctypes.byref(t)), "enomr_get_time")
+        return t.value
+
+    @time.setter
+    def time(self, t):
+        self._stream()
+        _check(_lib.enomr_set_time(self._ctx, float(t)), "enomr_set_time")
 
     def check_status(self):
         self._stream()
