@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--cfl", type=float, default=0.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--paper-runs", action="store_true",
+                    help="also time the paper's 2D problems as whole runs (about 2.5 min)")
     ap.add_argument("--only", choices=["adjoint", "batched", "vortex"], default=None,
                     help="run one secondary measurement alone (profiling aid)")
     return ap.parse_args()
@@ -582,6 +584,7 @@ def main_ours(a):
                                    "fp64_op_frac": sweep_fracs(enomr, sv, Uvd, R, n, a.cfl,
                                                                peak_ops)}
         sv.close()
+    if rank == 0 and not a.no_extras and a.paper_runs:
         # the paper's 2D problems (Sec. 4.4), whole runs with their CFL steps
         U1, d1, _ = workloads.riemann2d_rp1(801)
         extras["paper_rp1_801"] = paper_run(enomr, dev, "2D Riemann RP1, 801^2", U1, d1, d1, R,
@@ -594,6 +597,7 @@ def main_ours(a):
         extras["paper_rayleigh_taylor"] = paper_run(enomr, dev, "Rayleigh-Taylor, 200x800",
                                                     Ur_, rdx, rdy, R, rsides, (0.0, 1.0),
                                                     5.0 / 3.0, 0.3, 1.95)
+    if rank == 0 and not a.no_extras:
         adv = {}
         for Rk in (5, 9, 17):
             ua, ha = workloads.advection_sine(1 << 24)
