@@ -126,19 +126,21 @@ def sweep_work(order, C, sel, n_interfaces, counts, stage_epilogue=False):
 
     every interface (one per cell of the line):
       the cell's primitives and normal flux        15, 18 / 12, 14
-      Roe eigen-quantities and scaled rows of L    16, 19 / 15, 17
-      back-projection F = R (f^+ + f^-)            19, 24 / 16, 19
       flux difference of the cell                  2C, 2C
       stage update when the sweep carries it       4C, 6C (add of the other
                                                    sweep, 2 fma, 1 mul)
+    flat interfaces with bitwise-equal centre states (both sides take
+    S(0,0) on one state U, whose flux R L F(U) = F(U) is the cell's flux):
+      nothing more
+    every other interface:
+      Roe eigen-quantities and scaled rows of L    16, 19 / 15, 17
+      back-projection F = R (f^+ + f^-)            19, 24 / 16, 19
     the Roe average, where the centre states differ 11, 14 / 8, 10
-    flat interfaces (both sides: three equal cell states at the side's
-    centre, so IS_0 = 0 exactly and minmod returns v(0)):
-      projection of the centre cells               20, 40 / 12, 24 each
-                                                   (one projection when the
-                                                   two centre states are equal)
+    other flat interfaces (both sides: three equal cell states at the
+    side's centre, so IS_0 = 0 exactly and minmod returns v(0)):
+      projection of the two centre cells           20, 40 / 12, 24 each
       per field: two split fmas and f^+ + f^-      3, 5
-    other interfaces:
+    the remaining interfaces:
       projection of the 2g-cell window             20, 40 / 12, 24 per cell
       per field: split of 2(2g-1) values and f^+ + f^-
       per window (2C): the baseline indicator      6, 8
@@ -157,13 +159,14 @@ def sweep_work(order, C, sel, n_interfaces, counts, stage_epilogue=False):
                       for t in range(T)], dtype=np.float64)
     four = C == 4
     proj = np.array([20, 40] if four else [12, 24], dtype=np.float64)
-    fixed = (np.array([15, 18] if four else [12, 14]) + np.array([16, 19] if four else [15, 17])
-             + np.array([19, 24] if four else [16, 19]) + 2 * C
+    fixed = (np.array([15, 18] if four else [12, 14]) + 2 * C
              + (np.array([4 * C, 6 * C]) if stage_epilogue else 0)).astype(np.float64)
+    eigen = (np.array([16, 19] if four else [15, 17])
+             + np.array([19, 24] if four else [16, 19])).astype(np.float64)
     roe_avg = np.array([11, 14] if four else [8, 10], dtype=np.float64)
-    w = float(n_interfaces) * fixed + float(n_interfaces - n_eq) * roe_avg
-    w += float(n_flat_eq) * proj + float(n_flat - n_flat_eq) * 2 * proj
-    w += float(n_flat) * C * np.array([3, 5])
+    w = float(n_interfaces) * fixed + float(n_interfaces - n_flat_eq) * eigen
+    w += float(n_interfaces - n_eq) * roe_avg
+    w += float(n_flat - n_flat_eq) * (2 * proj + C * np.array([3, 5]))
     split = np.array([2 * (2 * g - 1) + 1, 4 * (2 * g - 1) + 1], dtype=np.float64)
     w += float(n_interfaces - n_flat) * (proj * 2 * g + C * split)
     cum = np.stack([np.cumsum(sizes), np.cumsum(2 * sizes - 1)], axis=1)  # walk to t
@@ -392,6 +395,57 @@ def paper_run(enomr, dev, name, U0, dx, dy, order, sides, gravity, gamma, cfl, t
             "steps": n, "t_reached": t, "status": status, "wall_s": round(el, 3),
             "unit": UNIT, "value": nx * ny * 3 * n / el,
             "note": "host-timed whole run; each step reads its CFL dt back to the host"}
+
+
+def end_to_end(s, U0, U, cells, a):
+    """The public step with host buffers: every step copies its input state
+    from pinned host memory and reads its result back.  The steps are
+    independent problems (each starts from the same host state), so the
+    copies run double-buffered on two copy streams and overlap the compute of
+    the neighbouring steps, as a caller streaming problems through one solver
+    would run them.  The serial form (copy in, step, copy out on one stream)
+    is timed beside it."""
+    import torch
+    dev = U.device
+    Uh_in = torch.from_numpy(U0).pin_memory()
+    Uh_out = [torch.empty_like(Uh_in).pin_memory() for _ in range(2)]
+    bufs = [torch.empty_like(U) for _ in range(2)]
+    comp = torch.cuda.current_stream(dev)
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    loaded, stepped, freed = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+    for b in range(2):
+        freed[b].record(comp)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        b = k % 2
+        with torch.cuda.stream(s_in):
+            s_in.wait_event(freed[b])           # the read-back of step k-2 is done
+            bufs[b].copy_(Uh_in, non_blocking=True)
+            loaded[b].record(s_in)
+        comp.wait_event(loaded[b])
+        s.step(bufs[b], 0.0, a.cfl)
+        stepped[b].record(comp)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(stepped[b])
+            Uh_out[b].copy_(bufs[b], non_blocking=True)
+            freed[b].record(s_out)
+    torch.cuda.synchronize()
+    overlapped = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        bufs[0].copy_(Uh_in, non_blocking=True)
+        s.step(bufs[0], 0.0, a.cfl)
+        Uh_out[0].copy_(bufs[0], non_blocking=True)
+    torch.cuda.synchronize()
+    serial = time.perf_counter() - t0
+    return {"value": cells * 3 * a.steps / overlapped, "unit": UNIT,
+            "h2d_bytes_per_step": Uh_in.numel() * 8,
+            "d2h_bytes_per_step": Uh_out[0].numel() * 8,
+            "copies": "double-buffered on two copy streams, overlapping the neighbouring "
+                      "steps' compute; host-timed over all steps",
+            "serial_value": cells * 3 * a.steps / serial}
 
 
 def aggregate_ranks(ms_local, cell_updates_per_rank, device):
@@ -629,21 +683,7 @@ def main_ours(a):
                                   "unit": UNIT, "values": burg}
         extras["batched"] = batched_gain(enomr, workloads, dev, a)
         extras["adjoint"] = adjoint_ratio(enomr, workloads, dev)
-        # end to end through the public API with host buffers
-        Uh_in = torch.from_numpy(U0).pin_memory()
-        Uh_out = torch.empty_like(Uh_in).pin_memory()
-        Ue = torch.empty_like(U)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(a.steps):
-            Ue.copy_(Uh_in, non_blocking=True)
-            s.step(Ue, 0.0, a.cfl)
-            Uh_out.copy_(Ue, non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        extras["e2e"] = {"value": cells * 3 * a.steps / e2e_s, "unit": UNIT,
-                         "h2d_bytes_per_step": Uh_in.numel() * 8,
-                         "d2h_bytes_per_step": Uh_out.numel() * 8}
+        extras["e2e"] = end_to_end(s, U0, U, cells, a)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

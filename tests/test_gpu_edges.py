@@ -96,3 +96,37 @@ def test_one_cell_wide_2d_grids(E, shape):
     forced = oracle.rhs_euler2d(U, dx, dy, R, bc=oracle.BC_TRANSMISSIVE, forced=sel)["rhs"]
     assert_values(got, forced, euler_flux_scale(U) / min(dx, dy), f"2d {shape}")
     s.check_status()
+
+
+@pytest.mark.parametrize("R", [5, 9, 17])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_uniform_state_is_steady(E, R, bc):
+    """A uniform state is a steady solution.  Every interface is flat with
+    equal centre states, both sides take S(0,0) and the flux R (f^+ + f^-)
+    is F(U) (exactly so on the GPU, which takes the cell's own flux there),
+    so the RHS is exactly zero on the GPU and zero up to rounding in the
+    oracle; one step keeps the state to within an ulp (the SSP-RK3 weights
+    round)."""
+    import torch
+    g = (R + 1) // 2
+    for ndim in (1, 2):
+        if ndim == 1:
+            N = max(3 * g, 40)
+            U = wl.conserved_1d(np.full(N, 1.3), np.full(N, 0.4), np.full(N, 2.1))
+            s = E.Solver(E.EULER, N, order=R, dx=0.1, bc=bc)
+            ref = oracle.rhs_euler1d(U, 0.1, R, bc=bc, want_sel=True)
+        else:
+            ny, nx = 70, 130
+            U = wl.conserved_2d(np.full((ny, nx), 1.3), 0.4, -0.7, 2.1)
+            s = E.Solver(E.EULER, (ny, nx), order=R, dx=0.1, dy=0.2, bc=bc)
+            ref = oracle.rhs_euler2d(U, 0.1, 0.2, R, bc=bc, want_sel=True)
+        Ud = dev(U)
+        sel = s.selection(Ud).cpu().numpy()
+        T = oracle.num_tested(R)
+        assert (sel == T + 2).all() and (ref["sel"] == T + 2).all()
+        rhs = s.rhs(Ud)
+        assert torch.count_nonzero(rhs) == 0
+        assert_values(rhs.cpu().numpy(), ref["rhs"], euler_flux_scale(U) / 0.1, "uniform")
+        s.step(Ud, dt=0.01)
+        assert np.abs(Ud.cpu().numpy() - U).max() <= 2e-16 * np.abs(U).max()
+        s.check_status()
