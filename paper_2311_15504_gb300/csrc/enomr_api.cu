@@ -63,79 +63,118 @@ namespace enomr {
 // ---------------------------------------------------------------------------
 // alpha_k per line (reading of Eq. LF_Flux_Split for systems: per
 // characteristic field, max over the cells of the line) and the CFL
-// wave-speed maximum.  Tile: 32 columns x 32 rows, 256 threads.
+// wave-speed maximum.  Tile: 32 columns x 32 rows, 256 threads; thread
+// (tx, ty) reads rows 4 ty .. 4 ty + 3 of column tx.
 // Maxima of non-negative doubles are taken on their bit patterns.
+//
+// Only representative cells are evaluated.  A cell whose state is bitwise
+// equal to its left neighbour's has that neighbour's speeds: it changes
+// neither its row's maxima nor the CFL maximum.  One equal to the cell above
+// changes none of its column's maxima.  So each row's maxima are attained
+// at a row representative (the first cell of its tile row, or one that
+// differs from its left neighbour) and each column's at a column
+// representative (likewise along the column); every other cell is skipped
+// (a constant region costs one evaluation per tile row and column), and so
+// is its status check, which its equal neighbour's covers.  The
+// representatives are compacted into a list that whole warps evaluate, so
+// skipped cells take no FP64 issue slots.  Every evaluated cell updates its
+// row, its column and the CFL maximum with its own speeds: the results are
+// the maxima over all cells, bit for bit.
 // ---------------------------------------------------------------------------
 template <int C>
 __global__ void __launch_bounds__(256) k_alpha(AlphaArgs A)
 {
-    __shared__ unsigned long long scol[8][32][3];
-    __shared__ unsigned long long sred[8];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    __shared__ unsigned long long srow[32][3], scol[32][3], scfl;
+    __shared__ unsigned short list[1024];  // tile cell index: row * 32 + column
+    __shared__ int nlist;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const long long x = (long long)blockIdx.x * 32 + tx;
+    const long long ty0 = (long long)blockIdx.y * 32, y0 = ty0 + 4 * ty;
     const long long ncell = A.nx * A.ny;
-    unsigned long long cm[3] = {0, 0, 0}, smx = 0;
-    for (int r = 0; r < 4; ++r) {
-        const long long y = (long long)blockIdx.y * 32 + ty + 8 * r;
-        unsigned long long rm[3] = {0, 0, 0};
-        if (x < A.nx && y < A.ny) {
-            const long long i = y * A.nx + x;
+    if (tid < 96) {
+        srow[tid / 3][tid % 3] = 0;
+        scol[tid / 3][tid % 3] = 0;
+    }
+    if (tid == 0) {
+        scfl = 0;
+        nlist = 0;
+    }
+    // the cell above this thread's first row (inside the tile for ty > 0)
+    double up[C] = {};
+    bool have_up = false;
+    if (C == 4 && ty > 0 && x < A.nx && y0 < A.ny) {
+        const long long i = (y0 - 1) * A.nx + x;
+#pragma unroll
+        for (int q = 0; q < C; ++q) up[q] = A.U[q * ncell + i];
+        have_up = true;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const long long y = y0 + j;
+        const bool valid = x < A.nx && y < A.ny;
+        double u[C];
+#pragma unroll
+        for (int q = 0; q < C; ++q) u[q] = valid ? A.U[q * ncell + y * A.nx + x] : 0.0;
+        bool same_left = tx > 0;
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            const double l = __shfl_up_sync(0xffffffffu, u[q], 1);
+            same_left = same_left && (__double_as_longlong(l) == __double_as_longlong(u[q]));
+        }
+        bool rep = valid && !same_left;
+        if (C == 4) {
+            bool same_up = j > 0 || have_up;
+#pragma unroll
+            for (int q = 0; q < C; ++q)
+                same_up = same_up && (__double_as_longlong(up[q]) == __double_as_longlong(u[q]));
+            rep = rep || (valid && !same_up);
+#pragma unroll
+            for (int q = 0; q < C; ++q) up[q] = u[q];
+        }
+        const unsigned need = __ballot_sync(0xffffffffu, rep);
+        if (need) {
+            int base = 0;
+            if (tx == 0) base = atomicAdd(&nlist, __popc(need));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (rep)
+                list[base + __popc(need & ((1u << tx) - 1u))] =
+                    (unsigned short)((4 * ty + j) * 32 + tx);
+        }
+    }
+    __syncthreads();
+    const int n = nlist;
+    for (int b = ty * 32; b < n; b += 256) {
+        const int t = b + tx;
+        if (t < n) {
+            const int e = list[t], r = e >> 5, cx = e & 31;
+            const long long i = (ty0 + r) * A.nx + (long long)blockIdx.x * 32 + cx;
             const CellWaves cw = cell_waves<C>(A.U[i], A.U[ncell + i],
                                                (C == 4) ? A.U[2 * ncell + i] : 0.0,
                                                A.U[(C - 1) * ncell + i], A.gm1, A.gamma, A.status);
             const double u = cw.u, v = cw.v, c = cw.c;
-            rm[0] = __double_as_longlong(fabs(__dsub_rn(u, c)));
-            rm[1] = __double_as_longlong(fabs(u));
-            rm[2] = __double_as_longlong(fabs(__dadd_rn(u, c)));
+            atomicMax(&srow[r][0], (unsigned long long)__double_as_longlong(fabs(__dsub_rn(u, c))));
+            atomicMax(&srow[r][1], (unsigned long long)__double_as_longlong(fabs(u)));
+            atomicMax(&srow[r][2], (unsigned long long)__double_as_longlong(fabs(__dadd_rn(u, c))));
             if (C == 4) {
-                unsigned long long y0 = __double_as_longlong(fabs(__dsub_rn(v, c)));
-                unsigned long long y1 = __double_as_longlong(fabs(v));
-                unsigned long long y2 = __double_as_longlong(fabs(__dadd_rn(v, c)));
-                cm[0] = cm[0] > y0 ? cm[0] : y0;
-                cm[1] = cm[1] > y1 ? cm[1] : y1;
-                cm[2] = cm[2] > y2 ? cm[2] : y2;
+                atomicMax(&scol[cx][0], (unsigned long long)__double_as_longlong(fabs(__dsub_rn(v, c))));
+                atomicMax(&scol[cx][1], (unsigned long long)__double_as_longlong(fabs(v)));
+                atomicMax(&scol[cx][2], (unsigned long long)__double_as_longlong(fabs(__dadd_rn(v, c))));
             }
             double s = __dmul_rn(__dadd_rn(fabs(u), c), A.inv_dx);
             if (C == 4) s = __fma_rn(__dadd_rn(fabs(v), c), A.inv_dy, s);
-            unsigned long long sb = __double_as_longlong(s);
-            smx = smx > sb ? smx : sb;
+            atomicMax(&scfl, (unsigned long long)__double_as_longlong(s));
         }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            unsigned long long m = rm[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                unsigned long long w = __shfl_xor_sync(0xffffffffu, m, o);
-                m = m > w ? m : w;
-            }
-            rm[k] = m;
-        }
-        if (tx == 0 && y < A.ny)
-            for (int k = 0; k < 3; ++k)
-                atomicMax((unsigned long long *)(A.ax + 3 * y + k), rm[k]);
     }
-    if (C == 4) {
-        for (int k = 0; k < 3; ++k) scol[ty][tx][k] = cm[k];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long w = __shfl_xor_sync(0xffffffffu, smx, o);
-        smx = smx > w ? smx : w;
-    }
-    if (tx == 0) sred[ty] = smx;
     __syncthreads();
-    if (C == 4 && ty == 0 && x < A.nx) {
-        for (int k = 0; k < 3; ++k) {
-            unsigned long long m = scol[0][tx][k];
-            for (int j = 1; j < 8; ++j) m = m > scol[j][tx][k] ? m : scol[j][tx][k];
-            atomicMax((unsigned long long *)(A.ay + 3 * x + k), m);
-        }
+    if (tid < 32) {
+        const long long y = ty0 + tid;
+        if (y < A.ny)
+            for (int k = 0; k < 3; ++k) atomicMax((unsigned long long *)(A.ax + 3 * y + k), srow[tid][k]);
+        if (C == 4 && x < A.nx)
+            for (int k = 0; k < 3; ++k) atomicMax((unsigned long long *)(A.ay + 3 * x + k), scol[tid][k]);
     }
-    if (threadIdx.x == 0 && A.smax) {
-        unsigned long long m = sred[0];
-        for (int j = 1; j < 8; ++j) m = m > sred[j] ? m : sred[j];
-        atomicMax((unsigned long long *)A.smax, m);
-    }
+    if (tid == 0 && A.smax) atomicMax((unsigned long long *)A.smax, scfl);
 }
 
 // First cell (smallest index along its line) whose wave speed equals the
