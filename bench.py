@@ -124,8 +124,10 @@ def sweep_work(order, C, sel, n_interfaces, counts, stage_epilogue=False):
     Sign flips, |x|, min/max and compares, which the kernels do on the
     integer ALU, count 0.  (ops, flops) per part, C = 4 / C = 3:
 
-    every interface (one per cell of the line):
+    every cell that differs from its predecessor along the line (a cell
+    equal to it repeats its values):
       the cell's primitives and normal flux        15, 18 / 12, 14
+    every interface (one per cell of the line):
       flux difference of the cell                  2C, 2C
       stage update when the sweep carries it       4C, 6C (add of the other
                                                    sweep, 2 fma, 1 mul)
@@ -150,21 +152,23 @@ def sweep_work(order, C, sel, n_interfaces, counts, stage_epilogue=False):
         (|S|, 2|S|-1) or the minmod fma (1, 2).
     sel: selection histogram counts[T+3] over all windows of the launch
     (flat interfaces included); counts: (flat, flat with equal centre
-    states, equal centre states) interface counts."""
+    states, equal centre states) interface counts and the number of cells
+    that differ from their predecessor along the line."""
     import oracle  # table sizes only
-    n_flat, n_flat_eq, n_eq = counts
+    n_flat, n_flat_eq, n_eq, n_distinct = counts
     g = (order + 1) // 2
     T = oracle.num_tested(order)
     sizes = np.array([oracle.candidate(order, t)[0] + oracle.candidate(order, t)[1] + 1
                       for t in range(T)], dtype=np.float64)
     four = C == 4
     proj = np.array([20, 40] if four else [12, 24], dtype=np.float64)
-    fixed = (np.array([15, 18] if four else [12, 14]) + 2 * C
-             + (np.array([4 * C, 6 * C]) if stage_epilogue else 0)).astype(np.float64)
+    cell = np.array([15, 18] if four else [12, 14], dtype=np.float64)
+    fixed = (2 * C + (np.array([4 * C, 6 * C]) if stage_epilogue else np.zeros(2))).astype(np.float64)
     eigen = (np.array([16, 19] if four else [15, 17])
              + np.array([19, 24] if four else [16, 19])).astype(np.float64)
     roe_avg = np.array([11, 14] if four else [8, 10], dtype=np.float64)
-    w = float(n_interfaces) * fixed + float(n_interfaces - n_flat_eq) * eigen
+    w = float(n_distinct) * cell + float(n_interfaces) * fixed
+    w += float(n_interfaces - n_flat_eq) * eigen
     w += float(n_interfaces - n_eq) * roe_avg
     w += float(n_flat - n_flat_eq) * (2 * proj + C * np.array([3, 5]))
     split = np.array([2 * (2 * g - 1) + 1, 4 * (2 * g - 1) + 1], dtype=np.float64)
@@ -185,7 +189,9 @@ def sweep_work(order, C, sel, n_interfaces, counts, stage_epilogue=False):
 def flat_interfaces(U, axis):
     """Interface counts of a transmissive 2D sweep (axis 0: x, 1: y):
     (flat, flat with bitwise-equal centre states, bitwise-equal centre
-    states), flatness in the sense of the kernel's shortcut."""
+    states), flatness in the sense of the kernel's shortcut, and the number
+    of cells that differ from their predecessor along the line (a line's
+    first cell included)."""
     import torch
     X = U if axis == 0 else U.transpose(1, 2)
     Xp = torch.nn.functional.pad(X.unsqueeze(0), (3, 3, 0, 0), mode="replicate")[0]
@@ -193,7 +199,10 @@ def flat_interfaces(U, axis):
     nI = X.shape[2] + 1
     e = [eq[:, o:o + nI] for o in range(5)]            # e_o: cells k-3+o, k-2+o
     flat = ((e[0] & e[1]) | (e[2] & e[3])) & ((e[3] & e[4]) | (e[1] & e[2]))
-    return (int(flat.sum().item()), int((flat & e[2]).sum().item()), int(e[2].sum().item()))
+    same_prev = (X[..., 1:] == X[..., :-1]).all(dim=0)
+    distinct = X.shape[1] + int((~same_prev).sum().item())
+    return (int(flat.sum().item()), int((flat & e[2]).sum().item()), int(e[2].sum().item()),
+            distinct)
 
 
 KERNEL_SOURCES = ("enomr_sweep.cuh", "enomr_kernels.cuh", "enomr_common.cuh", "gen_coeffs.py")
@@ -397,18 +406,47 @@ def paper_run(enomr, dev, name, U0, dx, dy, order, sides, gravity, gamma, cfl, t
             "note": "host-timed whole run; each step reads its CFL dt back to the host"}
 
 
-def end_to_end(s, U0, U, cells, a):
+def hbm_side(n, dom, avg_ms):
+    """The dominant sweep against HBM: its compulsory bytes per launch (x
+    sweep: read U, write D; y sweep: read U, D and U^n, write the stage
+    output, U^n = U in the first of the three stages) over its mean launch
+    time, and that rate over the measured copy bandwidth."""
+    state = 4 * 8 * n * n
+    compulsory = 2 * state if dom == 0 else state * (3 + 4 + 4) / 3.0
+    rate = compulsory / (avg_ms * 1e-3) / 1e9
+    peak = None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            peak = json.load(f).get("hbm_gbs")
+    return {"compulsory_bytes_per_launch": compulsory, "achieved_gbs": round(rate, 1),
+            "peak_gbs": peak, "frac": round(rate / peak, 4) if peak else None,
+            "peak_source": "measured copy bandwidth" if peak else None}
+
+
+def end_to_end(s, U0, U, cells, a, nsnap=10):
     """The public step with host buffers: every step copies its input state
-    from pinned host memory and reads its result back.  The steps are
-    independent problems (each starts from the same host state), so the
+    from pinned host memory and reads its result back.  The inputs are
+    snapshots of the timed trajectory (block j of steps/nsnap steps starts
+    from the state at its first step), so the steps cost what the
+    trajectory's steps cost.  The steps are independent problems, so the
     copies run double-buffered on two copy streams and overlap the compute of
     the neighbouring steps, as a caller streaming problems through one solver
     would run them.  The serial form (copy in, step, copy out on one stream)
     is timed beside it."""
     import torch
     dev = U.device
-    Uh_in = torch.from_numpy(U0).pin_memory()
-    Uh_out = [torch.empty_like(Uh_in).pin_memory() for _ in range(2)]
+    m = -(-a.steps // nsnap)
+    Ut = torch.from_numpy(U0).to(dev)
+    snaps = []
+    for k in range(a.steps):
+        if k % m == 0:
+            h = torch.empty(Ut.shape, dtype=Ut.dtype, pin_memory=True)
+            h.copy_(Ut)
+            snaps.append(h)
+        s.step(Ut, 0.0, a.cfl)
+    del Ut
+    Uh_out = [torch.empty(U.shape, dtype=U.dtype, pin_memory=True) for _ in range(2)]
     bufs = [torch.empty_like(U) for _ in range(2)]
     comp = torch.cuda.current_stream(dev)
     s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
@@ -422,7 +460,7 @@ def end_to_end(s, U0, U, cells, a):
         b = k % 2
         with torch.cuda.stream(s_in):
             s_in.wait_event(freed[b])           # the read-back of step k-2 is done
-            bufs[b].copy_(Uh_in, non_blocking=True)
+            bufs[b].copy_(snaps[k // m], non_blocking=True)
             loaded[b].record(s_in)
         comp.wait_event(loaded[b])
         s.step(bufs[b], 0.0, a.cfl)
@@ -434,15 +472,17 @@ def end_to_end(s, U0, U, cells, a):
     torch.cuda.synchronize()
     overlapped = time.perf_counter() - t0
     t0 = time.perf_counter()
-    for _ in range(a.steps):
-        bufs[0].copy_(Uh_in, non_blocking=True)
+    for k in range(a.steps):
+        bufs[0].copy_(snaps[k // m], non_blocking=True)
         s.step(bufs[0], 0.0, a.cfl)
         Uh_out[0].copy_(bufs[0], non_blocking=True)
     torch.cuda.synchronize()
     serial = time.perf_counter() - t0
     return {"value": cells * 3 * a.steps / overlapped, "unit": UNIT,
-            "h2d_bytes_per_step": Uh_in.numel() * 8,
+            "h2d_bytes_per_step": U.numel() * 8,
             "d2h_bytes_per_step": Uh_out[0].numel() * 8,
+            "inputs": f"{len(snaps)} snapshots of the timed trajectory, each the input of "
+                      f"{m} consecutive steps",
             "copies": "double-buffered on two copy streams, overlapping the neighbouring "
                       "steps' compute; host-timed over all steps",
             "serial_value": cells * 3 * a.steps / serial}
@@ -552,8 +592,8 @@ def main_ours(a):
         Us = torch.from_numpy(U0).to(dev)
         hx = np.zeros(T + 3)
         hy = np.zeros(T + 3)
-        cx = np.zeros(3)
-        cy = np.zeros(3)
+        cx = np.zeros(4)
+        cy = np.zeros(4)
         ns = 0
         for it in range(a.steps):
             if it % every == 0:
@@ -569,6 +609,7 @@ def main_ours(a):
         wx = sweep_work(R, 4, hx, n * (n + 1), cx)
         wy = sweep_work(R, 4, hy, n * (n + 1), cy, stage_epilogue=True)
         extras["flat_interface_fraction"] = [cx[0] / (n * (n + 1)), cy[0] / (n * (n + 1))]
+        extras["distinct_cell_fraction"] = [cx[3] / (n * n), cy[3] / (n * n)]
         probe, _ = enomr.probe_fp64_fma(iters=20000, device=dev)
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
@@ -600,7 +641,8 @@ def main_ours(a):
             "x_sweep_ms": round(x_avg, 4), "y_sweep_ms": round(y_avg, 4),
             "x_sweep_frac": round(wx[1] / (x_avg * 1e-3) / peak_ops, 4),
             "y_sweep_frac": round(wy[1] / (y_avg * 1e-3) / peak_ops, 4),
-            "alpha_ms": round(a_ms / max(na_launch, 1), 4)}
+            "alpha_ms": round(a_ms / max(na_launch, 1), 4),
+            "hbm": hbm_side(n, dom, avg)}
         extras["selection_histogram_x"] = [round(float(v)) for v in hx]
         extras["work_samples"] = ns
         # every order on the same workload, a smooth workload, and the scalar

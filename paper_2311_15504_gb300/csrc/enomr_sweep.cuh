@@ -35,10 +35,22 @@ struct SweepSmem {
     double sU[C][NL][S];
     double sF[C][NL][S];
     double sP[4][NL][S];  // sqrt(rho), u_n, u_t, H
-    double sFh[C][NL][TP];
+    // the staging phase's arrays share storage with arrays of the later
+    // phases (separated from them by barriers)
+    union {
+        double sFh[C][NL][TP];
+        unsigned short rep[NL * S];  // staging: cell -> the representative it copies
+    };
     unsigned long long red[TP * NL / 32][3];
-    int list[TP * NL];  // interfaces (line * TP + p) that take the long path
+    union {
+        int list[TP * NL];             // interfaces (line * TP + p) that take the long path
+        unsigned short slist[NL * S];  // staging: representatives to evaluate
+    };
     int nlist;
+    int nrep;
+    static_assert(sizeof(unsigned short) * NL * S <= sizeof(double) * C * NL * TP &&
+                      sizeof(unsigned short) * NL * S <= sizeof(int) * TP * NL,
+                  "staging arrays must fit in the storage they share");
 };
 
 // State of ghost cell craw (< 0 or >= the line length) of line L, in
@@ -286,10 +298,32 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
     const long long nlines = (DIR == 0) ? ny : nx;
     const int tid = threadIdx.x;
 
-    if (tid == 0) sm.nlist = 0;
-    // ---- stage cells, primitives and physical fluxes (normal direction)
-    for (int idx = tid; idx < NL * S; idx += NT) {
-        int line, s;
+    if (tid == 0) {
+        sm.nlist = 0;
+        sm.nrep = 0;
+    }
+    __syncthreads();
+    // ---- stage cells, primitives and physical fluxes (normal direction).
+    // A staged cell bitwise equal to its predecessor along the line has the
+    // same primitives and flux: only representatives (a line's first cell
+    // within each warp's 32 staged cells, or one that differs from its
+    // predecessor) are evaluated, by whole warps from a compacted list, and
+    // the others copy their representative's values.  The staged values are
+    // those of evaluating every cell, bit for bit; a piecewise-constant
+    // region costs a few evaluations per tile instead of one per cell.
+    static_assert(32 % NL == 0, "lines per tile must divide the warp");
+    constexpr int NS = NL * S;
+    constexpr int PD = (DIR == 0) ? 1 : NL;  // lane distance to the predecessor
+    constexpr unsigned CLS = NL == 1 ? 0xffffffffu
+                           : NL == 2 ? 0x55555555u
+                           : NL == 4 ? 0x11111111u
+                           : NL == 8 ? 0x01010101u
+                           : NL == 16 ? 0x00010001u : 0x00000001u;  // lanes of one line (DIR 1)
+    const int lane = tid & 31;
+    for (int base = tid & ~31; base < NS; base += NT) {
+        const int idx = base + lane;
+        const bool act = idx < NS;
+        int line = 0, s = 0;
         if (DIR == 0) {
             line = idx / S;
             s = idx - line * S;
@@ -297,31 +331,96 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
             s = idx / NL;
             line = idx - s * NL;
         }
-        long long L = l0 + line;
-        if (L >= nlines) L = nlines - 1;
         double u[C];
-        const long long craw = x0 - g + s;
-        if (EXT && (craw < 0 || craw >= nlen)) {
-            side_cell<C, DIR>(A, craw, L, u);
-        } else {
-            const long long cell = ghost(craw, nlen, A.bc);
-            const long long gi = (DIR == 0) ? L * nx + cell : cell * nx + L;
 #pragma unroll
-            for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
+        for (int q = 0; q < C; ++q) u[q] = 0.0;
+        if (act) {
+            long long L = l0 + line;
+            if (L >= nlines) L = nlines - 1;
+            const long long craw = x0 - g + s;
+            if (EXT && (craw < 0 || craw >= nlen)) {
+                side_cell<C, DIR>(A, craw, L, u);
+            } else {
+                const long long cell = ghost(craw, nlen, A.bc);
+                const long long gi = (DIR == 0) ? L * nx + cell : cell * nx + L;
+#pragma unroll
+                for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
+            }
+            sU[0][line][s] = u[0];
+            sU[1][line][s] = u[QN];
+            if (C == 4) sU[2][line][s] = u[QT];
+            sU[C - 1][line][s] = u[C - 1];
         }
-        const StagedCell<C> sc_ = stage_cell<C>(u[0], u[QN], (C == 4) ? u[QT] : 0.0, u[C - 1], A.gm1);
-        if (!positive(u[0]) || !positive(sc_.p) || !below_1e300(u[C - 1]))
-            atomicOr(A.status, ST_NONPHYS_CELL);
-        sU[0][line][s] = u[0];
-        sU[1][line][s] = u[QN];
-        if (C == 4) sU[2][line][s] = u[QT];
-        sU[C - 1][line][s] = u[C - 1];
+        bool same = lane >= PD && s > 0;
 #pragma unroll
-        for (int q = 0; q < C; ++q) sF[q][line][s] = sc_.F[q];
-        sP[0][line][s] = sc_.sq;
-        sP[1][line][s] = sc_.un;
-        sP[2][line][s] = sc_.ut;
-        sP[3][line][s] = sc_.H;
+        for (int q = 0; q < C; ++q) {
+            const double pq = __shfl_up_sync(FULL, u[q], PD);
+            same = same && (__double_as_longlong(pq) == __double_as_longlong(u[q]));
+        }
+        const bool rep = act && !same;
+        const unsigned reps = __ballot_sync(FULL, rep);
+        // representative of this cell: the nearest representative lane at or
+        // below this one on the same line (a line's first lane is one)
+        unsigned m = reps & (lane == 31 ? FULL : ((2u << lane) - 1u));
+        if (DIR == 1) m &= CLS << (lane % NL);
+        if (act) sm.rep[idx] = (unsigned short)(base + 31 - __clz(m));
+        if (reps) {
+            int b0 = 0;
+            if (lane == 0) b0 = atomicAdd(&sm.nrep, __popc(reps));
+            b0 = __shfl_sync(FULL, b0, 0);
+            if (rep) sm.slist[b0 + __popc(reps & ((1u << lane) - 1u))] = (unsigned short)idx;
+        }
+    }
+    __syncthreads();
+    {
+        const int nrep = sm.nrep;
+        for (int b = tid & ~31; b < nrep; b += NT) {
+            const int t = b + lane;
+            if (t < nrep) {
+                const int idx = sm.slist[t];
+                int line, s;
+                if (DIR == 0) {
+                    line = idx / S;
+                    s = idx - line * S;
+                } else {
+                    s = idx / NL;
+                    line = idx - s * NL;
+                }
+                const double u0 = sU[0][line][s], uE = sU[C - 1][line][s];
+                const StagedCell<C> sc_ = stage_cell<C>(u0, sU[1][line][s],
+                                                        (C == 4) ? sU[2][line][s] : 0.0, uE, A.gm1);
+                if (!positive(u0) || !positive(sc_.p) || !below_1e300(uE))
+                    atomicOr(A.status, ST_NONPHYS_CELL);
+#pragma unroll
+                for (int q = 0; q < C; ++q) sF[q][line][s] = sc_.F[q];
+                sP[0][line][s] = sc_.sq;
+                sP[1][line][s] = sc_.un;
+                sP[2][line][s] = sc_.ut;
+                sP[3][line][s] = sc_.H;
+            }
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NS; idx += NT) {
+        const int r = sm.rep[idx];
+        if (r != idx) {
+            int line, s, lr, sr_;
+            if (DIR == 0) {
+                line = idx / S;
+                s = idx - line * S;
+                lr = r / S;
+                sr_ = r - lr * S;
+            } else {
+                s = idx / NL;
+                line = idx - s * NL;
+                sr_ = r / NL;
+                lr = r - sr_ * NL;
+            }
+#pragma unroll
+            for (int q = 0; q < C; ++q) sF[q][line][s] = sF[q][lr][sr_];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sP[q][line][s] = sP[q][lr][sr_];
+        }
     }
     __syncthreads();
 
@@ -363,7 +462,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
         // append the other valid interfaces, in lane order within each warp
         const unsigned need = __ballot_sync(FULL, valid && !flat);
         if (need) {
-            const int lane = tid & 31;
             int base = 0;
             if (lane == 0) base = atomicAdd(&sm.nlist, __popc(need));
             base = __shfl_sync(FULL, base, 0);
