@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--paper-runs", action="store_true",
                     help="also time the paper's 2D problems as whole runs (about 2.5 min)")
-    ap.add_argument("--only", choices=["adjoint", "batched", "vortex"], default=None,
+    ap.add_argument("--only", choices=["adjoint", "batched", "vortex", "paper"], default=None,
                     help="run one secondary measurement alone (profiling aid)")
     return ap.parse_args()
 
@@ -488,6 +488,22 @@ def end_to_end(s, U0, U, cells, a, nsnap=10):
             "serial_value": cells * 3 * a.steps / serial}
 
 
+def paper_runs(enomr, workloads, dev, R):
+    """The paper's 2D problems (Sec. 4.4), whole runs with their CFL steps."""
+    out = {}
+    U1, d1, _ = workloads.riemann2d_rp1(801)
+    out["paper_rp1_801"] = paper_run(enomr, dev, "2D Riemann RP1, 801^2", U1, d1, d1, R,
+                                     None, (0.0, 0.0), 1.4, 0.3, 1.0)
+    Ud_, ddx, ddy, dsides = workloads.double_mach(1200, 300)
+    out["paper_double_mach"] = paper_run(enomr, dev, "double Mach reflection, 1200x300",
+                                         Ud_, ddx, ddy, R, dsides, (0.0, 0.0), 1.4, 0.1, 0.2)
+    Ur_, rdx, rdy, rsides = workloads.rayleigh_taylor(200, 800)
+    out["paper_rayleigh_taylor"] = paper_run(enomr, dev, "Rayleigh-Taylor, 200x800",
+                                             Ur_, rdx, rdy, R, rsides, (0.0, 1.0),
+                                             5.0 / 3.0, 0.3, 1.95)
+    return out
+
+
 def aggregate_ranks(ms_local, cell_updates_per_rank, device):
     """Whole-job rate of independent replicas: the max over ranks of the
     timed region (ms) and all ranks' cell-updates divided by it."""
@@ -681,18 +697,7 @@ def main_ours(a):
                                                                peak_ops)}
         sv.close()
     if rank == 0 and not a.no_extras and a.paper_runs:
-        # the paper's 2D problems (Sec. 4.4), whole runs with their CFL steps
-        U1, d1, _ = workloads.riemann2d_rp1(801)
-        extras["paper_rp1_801"] = paper_run(enomr, dev, "2D Riemann RP1, 801^2", U1, d1, d1, R,
-                                            None, (0.0, 0.0), 1.4, 0.3, 1.0)
-        Ud_, ddx, ddy, dsides = workloads.double_mach(1200, 300)
-        extras["paper_double_mach"] = paper_run(enomr, dev, "double Mach reflection, 1200x300",
-                                                Ud_, ddx, ddy, R, dsides, (0.0, 0.0), 1.4, 0.1,
-                                                0.2)
-        Ur_, rdx, rdy, rsides = workloads.rayleigh_taylor(200, 800)
-        extras["paper_rayleigh_taylor"] = paper_run(enomr, dev, "Rayleigh-Taylor, 200x800",
-                                                    Ur_, rdx, rdy, R, rsides, (0.0, 1.0),
-                                                    5.0 / 3.0, 0.3, 1.95)
+        extras.update(paper_runs(enomr, workloads, dev, R))
     if rank == 0 and not a.no_extras:
         adv = {}
         for Rk in (5, 9, 17):
@@ -837,6 +842,8 @@ def main_only(a):
         out = adjoint_ratio(enomr, workloads, dev, n=a.n, steps=a.steps)
     elif a.only == "vortex":
         out = vortex_rate(enomr, workloads, dev, a)
+    elif a.only == "paper":
+        out = paper_runs(enomr, workloads, dev, a.order)
     else:
         out = batched_gain(enomr, workloads, dev, a)
     print(json.dumps({"only": a.only, **out}), flush=True)
