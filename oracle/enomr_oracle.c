@@ -983,6 +983,17 @@ int orc_rhs_euler2d_ext(long nx, long ny, const double *U, double dx, double dy,
                         double gamma, const double *sides, double t, double gx, double gy,
                         const uint8_t *forced, uint8_t *sel_out, double *win_out, double *rhs)
 {
+    /* a reflective side mirrors the g cells next to it: its lines (rows for
+     * the x sides, columns for the y sides) must hold at least g cells */
+    const order_t *o = get_order(R);
+    int sd;
+    if (!o) return ORC_EINVAL;
+    for (sd = 0; sides && sd < 4; ++sd) {
+        const double *d = sides + 12 * sd;
+        const long len = sd < 2 ? nx : ny;
+        if (((int)d[0] == SIDE_REFLECTIVE || (int)d[1] == SIDE_REFLECTIVE) && len < o->g)
+            return ORC_EINVAL;
+    }
     return rhs_euler2d(nx, ny, U, dx, dy, R, 1, gamma, NULL, NULL, NULL, NULL, NULL, NULL, forced,
                        sel_out, win_out, rhs, NULL, NULL, NULL, sides, t, gx, gy);
 }
