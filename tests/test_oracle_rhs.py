@@ -252,3 +252,23 @@ def test_lssp_coefficients_small_m_exact():
     assert oracle.lssp_coeffs(3) == pytest.approx([1 / 3, 0, 2 / 3], abs=3e-16)
     assert oracle.lssp_coeffs(4) == pytest.approx([0, 2 / 3, 0, 1 / 3], abs=3e-16)
     assert oracle.lssp_coeffs(2).tolist() == [0.0, 1.0]
+
+
+@pytest.mark.parametrize("R", [5, 13])
+def test_euler2d_transpose_symmetry(R):
+    """Exchanging x and y (transposing the grid, swapping the momenta and the
+    spacings) transposes the right-hand side with its momenta swapped: the y
+    sweep is the x sweep of the transposed problem.  Bit for bit, since the
+    oracle takes the same operations on either axis; a wrong index or
+    component in one sweep breaks it."""
+    rng = np.random.Generator(np.random.PCG64(R))
+    ny, nx = 23, 31
+    U = wl.conserved_2d(0.5 + rng.random((ny, nx)), rng.uniform(-1, 1, (ny, nx)),
+                        rng.uniform(-1, 1, (ny, nx)), 0.5 + rng.random((ny, nx)))
+    U[:, 5:9, :] = U[:, 5:6, :]  # some flat windows too
+    for bc in (oracle.BC_TRANSMISSIVE, oracle.BC_PERIODIC):
+        a = oracle.rhs_euler2d(U, 0.1, 0.07, R, bc=bc, want_sel=True)
+        V = U.transpose(0, 2, 1)[[0, 2, 1, 3]].copy()
+        b = oracle.rhs_euler2d(V, 0.07, 0.1, R, bc=bc, want_sel=True)
+        assert np.array_equal(b["rhs"], a["rhs"].transpose(0, 2, 1)[[0, 2, 1, 3]])
+        assert np.array_equal(b["sel_x"], a["sel_y"]) and np.array_equal(b["sel_y"], a["sel_x"])
