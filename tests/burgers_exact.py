@@ -42,3 +42,42 @@ def errors(u, h, t, lam=1.0):
     x = h * np.arange(n)
     e = np.abs(u - exact(x, t, lam))
     return (e.sum() + e[0]) / (n + 1), e.max()
+
+
+
+def _u0(xi):
+    return 1.0 + 0.5 * np.sin(np.pi * xi) ** 3
+
+
+def _U0(xi):
+    """A primitive of u0 (sin^3 = sin - sin cos^2)."""
+    c = np.cos(np.pi * xi)
+    return xi - 0.5 / np.pi * (c - c ** 3 / 3.0)
+
+
+def exact_entropy(x, t, m=20001):
+    """Entropy solution for lam = 1 at any t, shocks included, by the
+    Hopf-Lax formula for the convex flux u^2/2: u(x, t) = u0(xi*) with xi*
+    the minimiser of U0(xi) + (x - xi)^2 / (2 t), U0 a primitive of u0.  The
+    minimiser lies in [x - 1.5 t, x - 0.5 t] (the range of u0); it is taken
+    on a grid of m points there, then refined by Newton's method on
+    u0(xi) - (x - xi) / t = 0 (the first-order condition)."""
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    out = np.empty_like(x)
+    grid = np.linspace(-1.5 * t, -0.5 * t, m)
+    for i, xx in enumerate(x):
+        xi = xx + grid
+        G = _U0(xi) + (xx - xi) ** 2 / (2.0 * t)
+        z = xi[np.argmin(G)]
+        for _ in range(30):
+            s_, c_ = np.sin(np.pi * z), np.cos(np.pi * z)
+            f = _u0(z) - (xx - z) / t
+            df = 1.5 * np.pi * s_ * s_ * c_ + 1.0 / t
+            if df <= 0.0:
+                break
+            step = f / df
+            z -= step
+            if abs(step) < 1e-15:
+                break
+        out[i] = _u0(z)
+    return out

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
-from burgers_exact import dt_schedule, errors
+from burgers_exact import dt_schedule, errors, exact, exact_entropy
 from conftest import read_golden
 from paper_2311_15504_gb300 import workloads as wl
 
@@ -106,3 +106,62 @@ def test_mixed_sign_reflection_and_conservation(R):
     ref = np.roll(u[::-1], 1)
     rr = oracle.rhs_burgers(-ref, h, R)["rhs"]
     assert np.allclose(-np.roll(rr[::-1], 1), r, rtol=0, atol=1e-11 * np.abs(r).max())
+
+
+def test_entropy_solution_reference():
+    """The Hopf-Lax reference: equal to the characteristic solution before
+    the shock forms, mass-conserving after, and its shock moves at the
+    Rankine-Hugoniot speed (u_L + u_R) / 2, which is 1 for this data (the
+    data are odd about u = 1 around the shock)."""
+    x = np.linspace(0.0, 2.0, 64, endpoint=False)
+    assert np.abs(exact_entropy(x, 0.3) - exact(x, 0.3)).max() < 1e-13
+    n = 4000
+    xx = (np.arange(n) + 0.5) * 2.0 / n
+    pos = []
+    for t in (1.5, 2.0):
+        u = exact_entropy(xx, t)
+        assert abs(u.mean() * 2.0 - 2.0) < 1e-3  # midpoint rule across one jump
+        j = np.argmax(np.abs(np.diff(u)))
+        pos.append(0.5 * (xx[j] + xx[j + 1]))
+        uL, uR = u[j], u[j + 1]
+        assert abs(0.5 * (uL + uR) - 1.0) < 5e-3
+    assert abs((pos[1] - pos[0]) % 2.0 - 0.5) <= 2.0 * 2.0 / n
+
+
+def _shock_run(N, R, cfl=0.3, T=2.0):
+    u, h = wl.burgers_sine3(N)
+    P = oracle.Problem(oracle.EQ_BURGERS, R, N, dx=h, bc=oracle.BC_PERIODIC)
+    u0, t, n = u.copy(), 0.0, 0
+    while t < T and n < 100000:
+        dt = min(P.cfl_dt(u, cfl), T - t)
+        assert dt > 0.0
+        u = P.step_ssprk3(u, dt)
+        t += dt
+        n += 1
+    return u0, u, h
+
+
+@pytest.mark.parametrize("R", [5, 9, 13, 17])
+def test_shock_run_against_entropy_solution(R):
+    """Sec. 4.2's second run (h = 1/64, CFL 0.3, t = 2, a shock at x = 1)
+    against the exact entropy solution: L1 error, no new extrema, the shock
+    within two cells, the smooth part within 1e-3, mass conserved."""
+    N = 128
+    u0, u, h = _shock_run(N, R)
+    x = h * np.arange(N)
+    ex = exact_entropy(x, 2.0)
+    assert np.abs(u - ex).mean() < 5e-3
+    assert u.max() <= ex.max() + 1e-3 and u.min() >= ex.min() - 1e-3
+    j = np.argmax(np.abs(np.diff(u)))
+    assert abs(0.5 * (x[j] + x[j + 1]) - 1.0) <= 2 * h
+    far = np.abs(x - 1.0) > 6 * h
+    assert np.abs(u - ex)[far].max() < 1e-3
+    assert abs(u.sum() - u0.sum()) * h < 1e-11
+
+
+def test_shock_run_converges_at_first_order():
+    errs = []
+    for N in (128, 256, 512):
+        _, u, h = _shock_run(N, 9)
+        errs.append(np.abs(u - exact_entropy(h * np.arange(N), 2.0)).mean())
+    assert errs[1] < 0.6 * errs[0] and errs[2] < 0.6 * errs[1]
