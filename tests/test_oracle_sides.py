@@ -134,3 +134,42 @@ def test_paper_2d_problem_setups():
     assert sides[2][4] == pytest.approx(1 / 6)
     V, hx, hy, _ = wl.rayleigh_taylor(16, 64)
     assert V.shape == (4, 64, 16) and abs(hx - hy) < 1e-15
+
+
+def test_double_mach_incident_shock_where_the_exact_solution_puts_it():
+    """The double Mach reflection (Sec. 4.4) on 120 x 30 cells at CFL 0.1 to
+    t = 0.05: away from the wall (y >= 0.3) the Mach 10 incident shock is
+    the exact straight shock x = 1/6 + (y + 20 t)/sqrt(3), which the top
+    side's moving split also follows.  The oracle's shock (the crossing of
+    the mid density between the post- and pre-shock states) sits within one
+    cell of it in every row, the gas well ahead of it is the pre-shock state
+    and density and pressure stay positive."""
+    kinds = {"transmissive": oracle.SIDE_TRANSMISSIVE, "reflective": oracle.SIDE_REFLECTIVE,
+             "inflow": oracle.SIDE_INFLOW}
+    nx, ny, R, T = 120, 30, 9, 0.05
+    U, dx, dy, sides = wl.double_mach(nx, ny)
+    pre = U[:, -1, -1].copy()
+    sd = tuple(oracle.side(kinds[k0], s0, kinds[k1], s1, a, b) for k0, s0, k1, s1, a, b in sides)
+    P = oracle.Problem(oracle.EQ_EULER2D, R, nx, ny, dx=dx, dy=dy, bc=oracle.BC_TRANSMISSIVE)
+    t, n = 0.0, 0
+    while t < T and n < 5000:
+        dt = min(P.cfl_dt(U, 0.1), T - t)
+        assert dt > 0.0
+        U = oracle.step_euler2d_ext(U, dx, dy, R, dt, sides=sd, t=t)
+        t += dt
+        n += 1
+    rho = U[0]
+    p = 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / rho)
+    assert rho.min() > 0 and p.min() > 0
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dy
+    mid = 0.5 * (8.0 + 1.4)
+    for j in np.nonzero(y >= 0.3)[0]:
+        xs = 1.0 / 6.0 + (y[j] + 20.0 * T) / np.sqrt(3.0)
+        i = np.nonzero(rho[j] > mid)[0].max()
+        x_num = x[i] + dx * (rho[j, i] - mid) / (rho[j, i] - rho[j, i + 1])
+        assert abs(x_num - xs) <= dx, (y[j], x_num, xs)
+        # the captured shock is a few cells wide; its precursor decays by
+        # about a decade per cell and is below 1e-9 twelve cells ahead
+        ahead = x > xs + 12 * dx
+        assert np.allclose(U[:, j, ahead], pre[:, None], rtol=0, atol=1e-8)
