@@ -173,3 +173,31 @@ def test_double_mach_incident_shock_where_the_exact_solution_puts_it():
         # about a decade per cell and is below 1e-9 twelve cells ahead
         ahead = x > xs + 12 * dx
         assert np.allclose(U[:, j, ahead], pre[:, None], rtol=0, atol=1e-8)
+
+
+@pytest.mark.parametrize("R", [5, 9, 17])
+def test_rayleigh_taylor_rest_state_is_hydrostatic(R):
+    """The Rayleigh-Taylor set-up without its velocity perturbation is at
+    rest in hydrostatic balance: p is linear in y with dp/dy = rho g, and
+    the scheme reproduces linear data, so the pressure gradient cancels the
+    body force (0, rho g) to rounding in every cell more than g + 1 cells
+    from the density jump at y = 0.5 and from the inflow sides; the
+    x-momentum right-hand side is exactly zero.  With the force's sign
+    flipped the y-momentum right-hand side is 2 rho g there."""
+    kinds = {"transmissive": oracle.SIDE_TRANSMISSIVE, "reflective": oracle.SIDE_REFLECTIVE,
+             "inflow": oracle.SIDE_INFLOW}
+    gamma = 5.0 / 3.0
+    _, dx, dy, sides = wl.rayleigh_taylor(16, 128)
+    sd = tuple(oracle.side(kinds[k0], s0, kinds[k1], s1, a, b) for k0, s0, k1, s1, a, b in sides)
+    y = (np.arange(128) + 0.5) * dy
+    rho = np.repeat(np.where(y < 0.5, 2.0, 1.0)[:, None], 16, axis=1)
+    p = np.repeat(np.where(y < 0.5, 2.0 * y + 1.0, y + 1.5)[:, None], 16, axis=1)
+    U = wl.conserved_2d(rho, 0.0, 0.0, p, gamma)
+    g = (R + 1) // 2
+    far = (np.abs(y - 0.5) > (g + 1) * dy) & (y > (g + 1) * dy) & (y < 1.0 - (g + 1) * dy)
+    r = oracle.rhs_euler2d_ext(U, dx, dy, R, sides=sd, gravity=(0.0, 1.0), gamma=gamma)["rhs"]
+    assert np.abs(r[:, far]).max() <= 1e-12 * p.max() / dy
+    assert not np.any(r[1])
+    flipped = oracle.rhs_euler2d_ext(U, dx, dy, R, sides=sd, gravity=(0.0, -1.0),
+                                     gamma=gamma)["rhs"]
+    assert np.allclose(flipped[2, far], -2.0 * rho[far], rtol=1e-12)
