@@ -272,3 +272,41 @@ def test_euler2d_transpose_symmetry(R):
         b = oracle.rhs_euler2d(V, 0.07, 0.1, R, bc=bc, want_sel=True)
         assert np.array_equal(b["rhs"], a["rhs"].transpose(0, 2, 1)[[0, 2, 1, 3]])
         assert np.array_equal(b["sel_x"], a["sel_y"]) and np.array_equal(b["sel_y"], a["sel_x"])
+
+
+def test_rp1_rows_far_from_the_centre_evolve_as_the_1d_riemann_problem():
+    """The paper's first 2D Riemann configuration (Sec. 4.4): away from the
+    centre, each half-line interface is a 1D Riemann problem.  For y = 0.7 the
+    states either side of x = 0, (0.5323, 1.206, 0, 0.3) | (1.5, 0, 0, 1.5),
+    have v = 0.  The exact solution is a single left-moving shock (p* = 1.5
+    and u* = 0 to 1e-5: the right state is the shocked left state), and
+    nothing from y = 0 reaches the row in 20 short steps, so the 2D oracle's
+    row follows its 1D scheme on the same data, step for step (same dt), to
+    rounding, with its shock where the exact speed puts it."""
+    from riemann_exact import star_state
+    ps, us = star_state((0.5323, 1.206, 0.3), (1.5, 0.0, 1.5))
+    assert abs(ps - 1.5) < 1e-5 and abs(us) < 1e-5
+    n, R = 101, 9
+    U, h, _ = wl.riemann2d_rp1(n)
+    y = -1.0 + h * (np.arange(n) + 0.5)
+    j = int(np.argmin(np.abs(y - 0.7)))
+    row = U[:, j, :]
+    U1 = np.stack([row[0], row[1], row[3]])
+    dt, steps = 0.1 * h, 20
+    P2 = oracle.Problem(oracle.EQ_EULER2D, R, n, n, dx=h, dy=h, bc=oracle.BC_TRANSMISSIVE)
+    P1 = oracle.Problem(oracle.EQ_EULER1D, R, n, dx=h, bc=oracle.BC_TRANSMISSIVE)
+    for _ in range(steps):
+        U = P2.step_ssprk3(U, dt)
+        U1 = P1.step_ssprk3(U1, dt)
+    scale = np.abs(U1).max()
+    assert np.abs(U[0, j] - U1[0]).max() <= 1e-12 * scale
+    assert np.abs(U[1, j] - U1[1]).max() <= 1e-12 * scale
+    assert np.abs(U[3, j] - U1[2]).max() <= 1e-12 * scale
+    assert np.abs(U[2, j]).max() <= 1e-12 * scale
+    # the shock: the largest density jump of the row, within a cell of
+    # x = S t with the exact left-shock speed
+    rl, ul, pl = 0.5323, 1.206, 0.3
+    S = ul - np.sqrt(1.4 * pl / rl) * np.sqrt(2.4 / 2.8 * ps / pl + 0.4 / 2.8)
+    x = -1.0 + h * (np.arange(n) + 0.5)
+    k = int(np.argmax(np.abs(np.diff(U1[0]))))
+    assert abs(0.5 * (x[k] + x[k + 1]) - S * steps * dt) <= h
