@@ -347,7 +347,8 @@ def adjoint_ratio(enomr, workloads, dev, n=1024, order=9, steps=10, cfl=0.5):
 def sweep_fracs(enomr, solver, U, order, n, cfl, peak_ops, steps=2):
     """FP64-operation roofline fractions of the x and y sweeps of `steps`
     SSP-RK3 steps from state U (each sweep timed live on the library's
-    stream; work from the selections and flat-interface counts of U)."""
+    stream; work from the selections and flat-interface counts of U), and
+    their compulsory bytes against the measured HBM bandwidth."""
     import torch
     T = enomr.num_tested(order)
     nsx = 8 * n * (n + 1)
@@ -363,7 +364,10 @@ def sweep_fracs(enomr, solver, U, order, n, cfl, peak_ops, steps=2):
         for _ in range(steps):
             solver.step(Uc, 0.0, cfl)
         nl, ms = solver.profile_end()
-        out["x" if kind == 1 else "y"] = round(w[1] / (ms / max(nl, 1) * 1e-3) / peak_ops, 4)
+        key = "x" if kind == 1 else "y"
+        out[key] = round(w[1] / (ms / max(nl, 1) * 1e-3) / peak_ops, 4)
+        if ms > 0:  # the same launches against the measured copy bandwidth
+            out[key + "_hbm_frac"] = hbm_side(n, kind - 1, ms / max(nl, 1))["frac"]
     return out
 
 
