@@ -21,8 +21,7 @@
  *   Sec. 4    Roe-averaged characteristic decomposition for Euler; 1D and
  *             2D Euler equations.
  *
- * Readings of places where the paper is silent or garbled (each is listed in
- * the design notes of the repository):
+ * Readings of places where the paper is silent or garbled:
  *   - Candidate list for order R = 2r-1 < 17: the entries of Eq. (Candidates)
  *     with m <= r-1 and n <= r-1, kept in the printed order.
  *   - "smaller than" is strict; equality falls through.
