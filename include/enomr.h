@@ -173,7 +173,9 @@ typedef struct {
     double state_lo[4], state_hi[4];
 } enomr_side;
 
-/* enomr_set_side -- set one side (copied; synchronous).  ENOMR_EINVAL for a
+/* enomr_set_side -- set one side (copied; synchronous: waits for the work
+ * already queued on the context's stream, which may read the sides, before
+ * it replaces them).  ENOMR_EINVAL for a
  * context that is not 2D Euler with transmissive boundaries, a bad kind or
  * side, a reflective side across fewer than g cells, or a non-physical
  * inflow state. */
@@ -181,7 +183,8 @@ ENOMR_API enomr_status enomr_set_side(enomr_ctx *ctx, int side, const enomr_side
 
 /* enomr_set_body_force -- add S = (0, rho gx, rho gy, rho u gx + rho v gy)
  * to the right-hand side after the two directional flux differences
- * (2D Euler only); (0, 0) removes it. */
+ * (2D Euler only); (0, 0) removes it.  The first non-zero force of a
+ * context without sides waits for the work queued on its stream. */
 ENOMR_API enomr_status enomr_set_body_force(enomr_ctx *ctx, double gx, double gy);
 
 /* enomr_set_time / enomr_get_time -- the time of the state the next
@@ -330,10 +333,11 @@ ENOMR_API enomr_status enomr_probe_fp64_fma(void *stream, int64_t iters, double 
  * Result: dUdt equals enomr_rhs() of a context with the same parameters.
  * Scratch: the per-line alpha maxima and a status word live in one static
  * device array of the library (about 0.8 MB), held on every GPU that loads
- * the library until the process exits.  The first call on a device looks up
- * that array's device address (a host-side set-up step, done once per
- * device), so make the first call on each device before any stream
- * capture.  All calls share the array and it keeps the last call's
+ * the library until the process exits.  Each call made outside stream
+ * capture looks up that array's device address on the current device (a
+ * host-side step; a device reset may move the array), and calls made during
+ * capture reuse the address of the last call outside capture, so make the
+ * first call on each device before any stream capture.  All calls share the array and it keeps the last call's
  * contents (each call clears what must start at zero): calls that overlap
  * on the GPU -- on different streams, or from several host threads -- race
  * and give wrong results; serialise them.  Non-physical states are not

@@ -998,6 +998,9 @@ ENOMR_API enomr_status enomr_set_side(enomr_ctx *c, int side, const enomr_side *
     }
     if (d->split0 != d->split0 || d->split_rate != d->split_rate) return ENOMR_EINVAL;
     SideDev h[4];
+    // the sides are read by sweeps already queued on the context's stream,
+    // which may be a non-blocking one: let them finish before the copy
+    CU_TRY(cudaStreamSynchronize(c->stream));
     if (c->custom_sides) {
         CU_TRY(cudaMemcpy(h, c->sides_d, sizeof(h), cudaMemcpyDeviceToHost));
     } else {
@@ -1025,7 +1028,9 @@ ENOMR_API enomr_status enomr_set_body_force(enomr_ctx *c, double gx, double gy)
     if (!c || c->eq != ENOMR_EULER || c->ndim != 2) return ENOMR_EINVAL;
     if (gx != gx || gy != gy) return ENOMR_EINVAL;
     if ((gx != 0.0 || gy != 0.0) && !c->custom_sides) {
-        // the EXT sweeps read the sides: make them the default ones
+        // the EXT sweeps read the sides: make them the default ones (after
+        // the work already queued on the context's stream)
+        CU_TRY(cudaStreamSynchronize(c->stream));
         SideDev h[4];
         for (int i = 0; i < 4; ++i) {
             memset(&h[i], 0, sizeof(SideDev));

@@ -31,20 +31,29 @@ std::mutex g_setup_mutex;
 double *g_scratch_addr[kMaxDevices] = {};  // device address of g_scratch, per device
 
 // Device address of g_scratch on the current device.  In host code the name
-// g_scratch is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
-cudaError_t scratch_address(double **out)
+// g_scratch is only a host-side stand-in, so the address is looked up with
+// that device current.  It is looked up again on every call made outside
+// stream capture (a device reset reloads the module, and the array may then
+// sit elsewhere); during capture the address cached by the last call outside
+// capture on that device is used, so the first call on a device must come
+// before any capture.
+cudaError_t scratch_address(cudaStream_t s, double **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[dev] = static_cast<double *>(p);
+    } else if (!g_scratch_addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;
@@ -88,12 +97,12 @@ extern "C" ENOMR_API enomr_status enomr_rhs_euler2d_noalloc(const double *U, dou
     const int g = (order + 1) / 2;
     if (bc == ENOMR_PERIODIC && (nx < 2 * g || ny < 2 * g)) return ENOMR_EINVAL;
 
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     double *base = nullptr;
-    if (scratch_address(&base) != cudaSuccess) return ENOMR_ECUDA;
+    if (scratch_address(s, &base) != cudaSuccess) return ENOMR_ECUDA;
     double *ax = base;                 // [ny][3]
     double *ay = base + 3 * kMaxLines; // [nx][3]
     int *status = reinterpret_cast<int *>(base + 6 * kMaxLines);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     // the maxima accumulate with atomicMax and must start at zero
     if (cudaMemsetAsync(ax, 0, sizeof(double) * 3 * ny, s) != cudaSuccess ||

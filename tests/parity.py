@@ -7,7 +7,8 @@ within 1e-12 of the scale of the terms forming it (sum_l |b_l| max|v|), or
 a minmod decision whose compared slopes are within the same relative
 distance.  Values: the oracle is re-run with the CUDA path's selection
 forced, so every cell is compared, with the bound
-|d| <= 1e-12 * max(||L||_inf, ||F||_inf / h).
+|d| <= 1e-12 * max(||L||_inf, ||F||_inf / h), and |d| <= 1e-12 ||L||_inf
+where the flux term is small enough for that bound to be attainable.
 """
 from __future__ import annotations
 
@@ -17,6 +18,8 @@ import oracle
 
 TIE_REL = 1e-12
 VAL_REL = 1e-12
+# strict 1e-12 ||L||_inf bound where ||F||_inf / h <= STRICT_RATIO ||L||_inf
+STRICT_RATIO = 64.0
 
 
 def _bsum(R):
@@ -63,13 +66,35 @@ def assert_selection(R, sel_gpu, sel_orc, windows, what="", scale_fn=None):
     return n
 
 
-def assert_values(gpu, ref, flux_scale_over_h, what=""):
+def assert_values(gpu, ref, flux_scale_over_h, what="", strict=None):
+    """Bound |GPU - oracle| elementwise and return err / ||L||_inf.
+
+    The general bound is 1e-12 * max(||L||_inf, ||F||_inf / h): L is a
+    difference of two interface fluxes divided by h, so a rounding error of
+    a few ulps in F (the two sides' different operation orders) reaches
+    ~eps ||F||_inf / h in L however small L is.  On a fine grid of smooth
+    data ||F||_inf / h exceeds ||L||_inf by up to the number of cells per
+    wavelength, and there no bound in ||L||_inf alone can hold.  Where that
+    floor is far below the strict bound (||F||_inf / h <= STRICT_RATIO
+    ||L||_inf, the default of strict=None), |GPU - oracle| <= 1e-12
+    ||L||_inf is asserted as well.
+    """
     gpu = np.asarray(gpu)
     ref = np.asarray(ref)
-    scale = max(float(np.abs(ref).max()), float(flux_scale_over_h))
+    lnorm = float(np.abs(ref).max())
+    scale = max(lnorm, float(flux_scale_over_h))
     err = float(np.abs(gpu - ref).max())
+    rel_l = err / lnorm if lnorm > 0 else (0.0 if err == 0 else np.inf)
+    if strict is None:
+        strict = float(flux_scale_over_h) <= STRICT_RATIO * lnorm
+    print(f"{what}: max|d| = {err:.3e}, /||L|| = {rel_l:.2e}, "
+          f"/max(||L||,||F||/h) = {err / scale if scale > 0 else 0.0:.2e}"
+          f"{' (strict)' if strict else ''}")
     assert err <= VAL_REL * scale, f"{what}: max|d| = {err:.3e} > {VAL_REL:.0e} * {scale:.3e}"
-    return err / scale if scale > 0 else 0.0
+    if strict:
+        assert err <= VAL_REL * lnorm, (
+            f"{what}: max|d| = {err:.3e} > {VAL_REL:.0e} * ||L||_inf = {lnorm:.3e}")
+    return rel_l
 
 
 def euler_flux_scale(U, gamma=1.4):
@@ -154,3 +179,91 @@ def shock_gate(step_fn, U0, steps, seeds=(1, 2)):
             b = step_fn(b, dt)
         env = max(env, float(np.abs(b - base).mean()))
     return base, max(1e-6, 4.0 * env), env
+
+
+def forced_replay(stage_gpu, sel_gpu, to_host, rhs_forced, U0_dev, U0, steps, flips_fn=None):
+    """Advance the CUDA path and the oracle side by side with the CUDA path's
+    per-stage selections forced on the oracle.
+
+    Per SSP-RK3 step of size dt (Eq. TVD3rdRK, in the paper's written form):
+    the CUDA path takes its three stages explicitly (stage_gpu(s, Un, Us,
+    out, dt)), its selection at every stage state (sel_gpu) is handed to
+    the oracle's right-hand side (rhs_forced(V, sel)), and the oracle
+    combines its own stages.  With every discrete choice shared, the two
+    trajectories differ by rounding propagated through a Lipschitz map, not
+    by the selection flips that make free-running shock trajectories
+    diverge, so the final states can be compared at a fixed tolerance.
+
+    flips_fn(U_stage_host, sel), if given, counts the stage's flips against
+    the oracle's own selection on the CUDA path's stage state and asserts
+    that each is a near-tie; its counts are summed.  Returns (final CUDA
+    state, final oracle state, total flips, stage evaluations).
+    """
+    import torch
+    Un = U0_dev.clone()
+    U1, U2, U3 = torch.empty_like(Un), torch.empty_like(Un), torch.empty_like(Un)
+    V = np.array(U0, dtype=np.float64, copy=True)
+    flips = 0
+    nstage = 0
+    for dt in steps:
+        sels = []
+        for s, (Us, out) in enumerate(((Un, U1), (U1, U2), (U2, U3)), start=1):
+            sel = sel_gpu(Us)
+            if flips_fn is not None:
+                flips += flips_fn(to_host(Us), sel)
+            sels.append(sel)
+            stage_gpu(s, Un, Us, out, dt)
+            nstage += 1
+        V1 = V + dt * rhs_forced(V, sels[0])
+        V2 = 0.75 * V + 0.25 * (V1 + dt * rhs_forced(V1, sels[1]))
+        V = (1.0 / 3.0) * V + (2.0 / 3.0) * (V2 + dt * rhs_forced(V2, sels[2]))
+        Un, U3 = U3, Un
+    return to_host(Un), V, flips, nstage
+
+
+def classify_euler2d_flips(U, dx, dy, R, bc, sel, ref_sel, chunk=64, gamma=1.4):
+    """Classify every selection flip of a 2D Euler RHS (CUDA selections sel
+    against the oracle's ref_sel, both in the [x sweep | y sweep] layout of
+    enomr_debug_selection).  A sweep of a line depends on that line only,
+    so the oracle's windows are formed on stacks of at most `chunk` flipped
+    lines at a time (memory stays bounded on a 4096^2 grid).  Returns
+    (flips, near-ties, worst relative distance) summed over both sweeps."""
+    U = np.asarray(U)
+    _, ny, nx = U.shape
+    nsx = 8 * ny * (nx + 1)
+    sel = np.asarray(sel).reshape(-1)
+    ref_sel = np.asarray(ref_sel).reshape(-1)
+    flips = np.nonzero(sel != ref_sel)[0]
+    total = ties = 0
+    worst = 0.0
+    for sweep in ("x", "y"):
+        sub = flips[flips < nsx] if sweep == "x" else flips[flips >= nsx] - nsx
+        if sub.size == 0:
+            continue
+        nlen, nlines = (nx, ny) if sweep == "x" else (ny, nx)
+        lines = np.unique((sub // (nlen + 1)) % nlines)
+        gs = (sel[:nsx] if sweep == "x" else sel[nsx:]).reshape(2, 4, nlines, nlen + 1)
+        rs = (ref_sel[:nsx] if sweep == "x" else ref_sel[nsx:]).reshape(2, 4, nlines, nlen + 1)
+        for c0 in range(0, lines.size, chunk):
+            ln = lines[c0:c0 + chunk]
+            Ul = U[:, ln, :] if sweep == "x" else U[:, :, ln]
+            o = oracle.rhs_euler2d(np.ascontiguousarray(Ul), dx, dy, R, bc=bc, gamma=gamma,
+                                   want_sel=True, want_win=True)
+            L = ln.size
+            if sweep == "x":
+                osel, win = o["sel_x"], o["win_x"]
+                X = (lambda Ul_: lambda y: Ul_[:, y, :].T.copy())(Ul)
+                fn = euler_scale_fn(X, L, nlen, R, bc, (lambda o_: lambda y: o_["alpha_x"][y])(o),
+                                    gamma)
+            else:
+                osel, win = o["sel_y"], o["win_y"]
+                X = (lambda Ul_: lambda x: Ul_[[0, 2, 1, 3], :, x].T.copy())(Ul)
+                fn = euler_scale_fn(X, L, nlen, R, bc, (lambda o_: lambda x: o_["alpha_y"][x])(o),
+                                    gamma)
+            # the stacked lines' sweep equals the full problem's on those lines
+            assert np.array_equal(osel, rs[:, :, ln, :])
+            n, t, w = classify_mismatches(R, gs[:, :, ln, :], osel, win, fn)
+            total += n
+            ties += t
+            worst = max(worst, w)
+    return total, ties, worst

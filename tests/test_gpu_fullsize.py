@@ -3,14 +3,15 @@ configuration (the public API with the library's fixed tile shapes).
 
 The oracle evaluates every output here (its OpenMP loops make a 4096^2 RHS
 take seconds); values are compared with the oracle re-run on the CUDA
-path's selections, and selection flips (near-ties, see tests/parity.py)
-are counted and bounded.
+path's selections, and every selection flip is classified as a near-tie
+(tests/parity.py) and counted.
 """
 import numpy as np
 import pytest
 
 import oracle
-from parity import assert_selection, assert_values, euler_flux_scale, euler_scale_fn
+from parity import (assert_selection, assert_values, classify_euler2d_flips, euler_flux_scale,
+                    euler_scale_fn)
 from paper_2311_15504_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -42,37 +43,12 @@ def test_riemann2d_4096_order9(E):
     got = s.rhs(Ud).cpu().numpy()
     s.check_status()
     ref_sel = oracle.rhs_euler2d(U, dx, dy, R, bc=oracle.BC_TRANSMISSIVE, want_sel=True)["sel"]
-    flips = np.nonzero(ref_sel != sel)[0]
-    print(f"4096^2: selection flips {flips.size} of {sel.size}")
-    assert flips.size <= 1e-3 * sel.size
-    # classify a sample of the flips: a sweep of a line depends on that line
-    # only, so the oracle's windows come from the stacked sampled lines
-    nsx = 8 * n * (n + 1)
-    rng = np.random.Generator(np.random.PCG64(0))
-    for sweep, sub in (("x", flips[flips < nsx]), ("y", flips[flips >= nsx] - nsx)):
-        if sub.size == 0:
-            continue
-        lines = np.unique((sub // (n + 1)) % n)
-        lines = np.sort(rng.choice(lines, size=min(100, lines.size), replace=False))
-        Ul = U[:, lines, :] if sweep == "x" else U[:, :, lines]
-        o = oracle.rhs_euler2d(Ul, dx, dy, R, bc=oracle.BC_TRANSMISSIVE, want_sel=True,
-                               want_win=True)
-        L = lines.size
-        if sweep == "x":
-            gsel = sel[:nsx].reshape(2, 4, n, n + 1)[:, :, lines, :]
-            osel, win = o["sel_x"], o["win_x"]
-            X = lambda y: Ul[:, y, :].T.copy()  # noqa: E731
-            fn = euler_scale_fn(X, L, n, R, 1, lambda y: o["alpha_x"][y])
-        else:
-            gsel = sel[nsx:].reshape(2, 4, n, n + 1)[:, :, lines, :]
-            osel, win = o["sel_y"], o["win_y"]
-            X = lambda x: Ul[[0, 2, 1, 3], :, x].T.copy()  # noqa: E731
-            fn = euler_scale_fn(X, L, n, R, 1, lambda x: o["alpha_y"][x])
-        # the stacked lines' sweep equals the full problem's for those lines
-        ref_l = ref_sel[:nsx] if sweep == "x" else ref_sel[nsx:]
-        assert np.array_equal(osel, ref_l.reshape(2, 4, n, n + 1)[:, :, lines, :])
-        nflip = assert_selection(R, gsel, osel, win, f"4096^2 {sweep} sample", fn)
-        print(f"  {sweep}: {nflip} sampled flips, all near-ties")
+    n_fl, n_tie, worst = classify_euler2d_flips(U, dx, dy, R, oracle.BC_TRANSMISSIVE, sel,
+                                                ref_sel)
+    print(f"4096^2: selection flips {n_fl} of {sel.size}, {n_tie} near-ties "
+          f"(worst relative distance {worst:.2e})")
+    assert n_fl == n_tie, f"{n_fl - n_tie} flips that are not near-ties (worst {worst:.2e})"
+    assert n_fl <= 1e-3 * sel.size
     forced = oracle.rhs_euler2d(U, dx, dy, R, bc=oracle.BC_TRANSMISSIVE, forced=sel)["rhs"]
     assert_values(got, forced, euler_flux_scale(U) / dx, "4096^2 riemann")
 
@@ -88,8 +64,17 @@ def test_advection_2p24(E, R):
     sel = s.selection(ud).cpu().numpy()
     got = s.rhs(ud).cpu().numpy()
     ref = oracle.rhs_advection(u, h, R, want_sel=True)
-    flips = int((ref["sel"].reshape(-1) != sel).sum())
-    assert flips <= 1e-6 * sel.size
+    rs = ref["sel"].reshape(-1)
+    flips = np.nonzero(rs != sel)[0]
+    print(f"advection 2^24 R={R}: {flips.size} flips")
+    assert flips.size <= 1e-6 * sel.size
+    if flips.size:
+        # a = 1 > 0: f^+ = u, f^- = 0; the f^+ window of interface k (entry k
+        # of side 0) is u at cells k-1+l, so the f^- windows cannot flip
+        assert (flips < N + 1).all()
+        g = (R + 1) // 2
+        cells = (flips[:, None] - 1 + np.arange(-(g - 1), g)[None, :]) % N
+        assert_selection(R, sel[flips], rs[flips], u[cells], f"advection 2^24 R={R}")
     forced = oracle.rhs_advection(u, h, R, forced=sel)["rhs"]
     assert_values(got, forced, np.abs(u).max() / h, f"advection 2^24 R={R}")
 
