@@ -52,7 +52,7 @@ typedef enum {
     ENOMR_ENOMEM = 2,   /* scratch allocation failed in enomr_init          */
     ENOMR_ECUDA = 3,    /* a CUDA runtime call or launch failed             */
     ENOMR_ENONPHYS = 4, /* a kernel met a non-physical state (status word)  */
-    ENOMR_ETIMEOUT = 5  /* reserved: a bounded device wait gave up          */
+    ENOMR_ETIMEOUT = 5  /* a bounded device wait gave up (status word)      */
 } enomr_status;
 
 typedef enum { ENOMR_ADVECTION = 0, ENOMR_EULER = 1, ENOMR_BURGERS = 2 } enomr_eq;
@@ -212,8 +212,27 @@ ENOMR_API enomr_status enomr_get_time(enomr_ctx *ctx, double *t);
 ENOMR_API enomr_status enomr_debug_selection(enomr_ctx *ctx, const double *U, uint8_t *sel);
 
 /* enomr_get_status -- synchronise the stream, read and clear the device
- * status word: ENOMR_OK or ENOMR_ENONPHYS. */
+ * status word: ENOMR_OK, ENOMR_ENONPHYS, or ENOMR_ETIMEOUT when a sweep's
+ * bounded wait for a tile copy ran out (that launch stopped early and its
+ * output is incomplete). */
 ENOMR_API enomr_status enomr_get_status(enomr_ctx *ctx);
+
+/*
+ * enomr_set_staging -- how the 2D Euler sweeps bring a tile of cells (with
+ * its g-cell halos, Sec. 2.1) into shared memory:
+ *   ENOMR_STAGING_AUTO  (default) the Tensor Memory Accelerator where the
+ *                       state allows it (nx even, U 16-byte aligned, no
+ *                       boundary sides or body force), else plain loads;
+ *   ENOMR_STAGING_LOADS plain coalesced loads by the CTA's threads;
+ *   ENOMR_STAGING_TMA   the TMA path only: calls whose state does not allow
+ *                       it return ENOMR_EINVAL.
+ * The TMA sweeps are persistent (one CTA per resident slot, a two-slot ring
+ * of tile copies per CTA, the next tile's copy in flight during this
+ * tile's arithmetic); both stagings give the same results bit for bit.
+ * Host-only setting, no synchronisation.
+ */
+enum { ENOMR_STAGING_AUTO = 0, ENOMR_STAGING_LOADS = 1, ENOMR_STAGING_TMA = 2 };
+ENOMR_API enomr_status enomr_set_staging(enomr_ctx *ctx, int mode);
 
 /*
  * Adjoint.  With the discrete choices of the forward pass frozen -- the

@@ -1,11 +1,14 @@
 // enomr_api.cu -- host side of libenomr.so: context, argument checks,
 // per-line alpha / CFL reduction kernel and the RK3 stage sequencing.
 // The C ABI is declared in include/enomr.h.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "../../include/enomr.h"
@@ -42,6 +45,8 @@ struct enomr_ctx {
     bool custom_sides;
     double gx, gy;
     double *t_dev;
+    // staging of the 2D sweeps: ENOMR_STAGING_AUTO / _LOADS / _TMA
+    int staging;
 };
 
 static void prof_start(enomr_ctx *c, int k)
@@ -369,6 +374,58 @@ template <int R> struct E2YEF {
 template <int R> struct E2YF {
     static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler2d_y<R>(a, s); }
 };
+template <int R> struct E2XTF {
+    static cudaError_t run(const CUtensorMap &m, const SweepArgs &a, cudaStream_t s)
+    {
+        return launch_euler2d_x_tma<R>(m, a, s);
+    }
+};
+template <int R> struct E2YTF {
+    static cudaError_t run(const CUtensorMap &m, const SweepArgs &a, cudaStream_t s)
+    {
+        return launch_euler2d_y_tma<R>(m, a, s);
+    }
+};
+
+// cuTensorMapEncodeTiled from the driver, looked up once (nullptr if the
+// driver does not provide it: the sweeps then stage with plain loads).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of a 2D Euler state U [4][ny][nx] with the box of sweep dir.
+// A tile copy needs 16-byte aligned rows (nx even), a 16-byte aligned base
+// and 32-bit coordinates; otherwise false (the sweeps then use plain loads).
+static bool state_map(const enomr_ctx *c, const double *U, int dir, CUtensorMap *m)
+{
+    if ((c->nx & 1) || (reinterpret_cast<uintptr_t>(U) & 15) || c->nx > (1LL << 30) ||
+        c->ny > (1LL << 30))
+        return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, 4};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->nx * 8, (cuuint64_t)(c->nx * c->ny) * 8};
+    unsigned b[3];
+    tma_box(c->order, dir, b);
+    const cuuint32_t box[3] = {b[0], b[1], b[2]};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double *>(U), dims, strides, box,
+               es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 template <int R> struct VjpF {
     static cudaError_t run(const VjpArgs &a, int C, int dir, cudaStream_t s)
@@ -494,17 +551,24 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
         prof_stop(c, 1);
         return cu(e);
     }
-    // 2D: x sweep -> D, y sweep adds D and applies the epilogue
+    // 2D: x sweep -> D, y sweep adds D and applies the epilogue.  The plain
+    // sweeps stage their tiles by TMA where the state allows it (same
+    // results bit for bit); the EXT instances always load.
+    const bool ext = extended(c);
+    CUtensorMap mx, my;
+    const bool tma = !ext && c->staging != ENOMR_STAGING_LOADS && state_map(c, U, 0, &mx) &&
+                     state_map(c, U, 1, &my);
+    if (c->staging == ENOMR_STAGING_TMA && !tma) return ENOMR_EINVAL;
     SweepArgs ax = sweep_args(c, U, false);
     ax.sel = sel;
     ax.ft_out = ft;
     ax.epi.mode = EPI_STORE;
     ax.epi.out = c->D;
     ax.t_coef = t_coef;
-    const bool ext = extended(c);
     prof_start(c, 1);
-    cudaError_t e = ext ? by_order<E2XEF>(c->order, ax, c->stream)
-                        : by_order<E2XF>(c->order, ax, c->stream);
+    cudaError_t e = ext   ? by_order<E2XEF>(c->order, ax, c->stream)
+                    : tma ? by_order<E2XTF>(c->order, mx, ax, c->stream)
+                          : by_order<E2XF>(c->order, ax, c->stream);
     prof_stop(c, 1);
     CU_TRY(e);
     SweepArgs ay = sweep_args(c, U, true);
@@ -514,7 +578,9 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     ay.epi.Dprev = c->D;
     ay.t_coef = t_coef;
     prof_start(c, 2);
-    e = ext ? by_order<E2YEF>(c->order, ay, c->stream) : by_order<E2YF>(c->order, ay, c->stream);
+    e = ext   ? by_order<E2YEF>(c->order, ay, c->stream)
+        : tma ? by_order<E2YTF>(c->order, my, ay, c->stream)
+              : by_order<E2YF>(c->order, ay, c->stream);
     prof_stop(c, 2);
     return cu(e);
 }
@@ -833,7 +899,15 @@ ENOMR_API enomr_status enomr_get_status(enomr_ctx *c)
     CU_TRY(cudaStreamSynchronize(c->stream));
     CU_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
+    if (h & ST_TMA_TIMEOUT) return ENOMR_ETIMEOUT;
     return h ? ENOMR_ENONPHYS : ENOMR_OK;
+}
+
+ENOMR_API enomr_status enomr_set_staging(enomr_ctx *c, int mode)
+{
+    if (!c || mode < ENOMR_STAGING_AUTO || mode > ENOMR_STAGING_TMA) return ENOMR_EINVAL;
+    c->staging = mode;
+    return ENOMR_OK;
 }
 
 static enomr_status rhs_vjp_impl(enomr_ctx *c, const double *U, const double *Lbar, double *Ubar,

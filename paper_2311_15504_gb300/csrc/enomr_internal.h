@@ -7,8 +7,14 @@
 
 namespace enomr {
 
-// Status bits of the device status word.
-enum : int { ST_NONPHYS_CELL = 1, ST_NONPHYS_ROE = 2 };
+// Status bits of the device status word (ST_TMA_TIMEOUT: a bounded wait for
+// a tile copy of the TMA sweeps ran out and the launch stopped early).
+enum : int { ST_NONPHYS_CELL = 1, ST_NONPHYS_ROE = 2, ST_TMA_TIMEOUT = 8 };
+
+// Tile shapes of the sweeps (interfaces per line x lines per CTA).
+constexpr int E1_TP = 64;
+constexpr int X_TP = 128, X_NL = 2;
+constexpr int Y_TP = 64, Y_NL = 4;
 
 // Burgers sign flags (second word of AdvArgs::speed): some u < 0, some u > 0
 enum : unsigned long long { SGN_NEG = 1ULL, SGN_POS = 2ULL };
@@ -130,6 +136,24 @@ template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, cudaStream_t s
 template <int R> cudaError_t launch_euler2d_x_ext(const SweepArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler2d_y_ext(const SweepArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, cudaStream_t s);
+}  // namespace enomr
+
+// the sweeps staged by the Tensor Memory Accelerator (enomr_tma.cuh)
+struct CUtensorMap_st;
+namespace enomr {
+template <int R> cudaError_t launch_euler2d_x_tma(const CUtensorMap_st &map, const SweepArgs &a,
+                                                  cudaStream_t s);
+template <int R> cudaError_t launch_euler2d_y_tma(const CUtensorMap_st &map, const SweepArgs &a,
+                                                  cudaStream_t s);
+// Box extents {x, y, components} of the tile copies of the TMA sweeps: the
+// x sweep copies TP + 2g cells (an even count) of X_NL rows, the y sweep
+// Y_NL columns of TP + 2g - 1 cells; g = (order + 1) / 2.
+inline void tma_box(int order, int dir, unsigned box[3])
+{
+    box[0] = dir == 0 ? (unsigned)(X_TP + order + 1) : (unsigned)Y_NL;
+    box[1] = dir == 0 ? (unsigned)X_NL : (unsigned)(Y_TP + order);
+    box[2] = 4;
+}
 
 // Transpose-Jacobian product of one sweep (enomr_vjp.cuh).
 struct VjpArgs {

@@ -5,6 +5,7 @@
 
 #include "enomr_scalar.cuh"
 #include "enomr_sweep.cuh"
+#include "enomr_tma.cuh"
 #include "enomr_vjp.cuh"
 
 namespace enomr {
@@ -122,6 +123,27 @@ template <int R> cudaError_t launch_advection_vjp(const AdvArgs &a, const double
 
 template cudaError_t launch_sweep_vjp<ENOMR_R>(const VjpArgs &, int, int, cudaStream_t);
 template cudaError_t launch_advection_vjp<ENOMR_R>(const AdvArgs &, const double *, double *, double,
+                                                   cudaStream_t);
+
+}  // namespace enomr
+
+namespace enomr {
+
+template <int R> cudaError_t launch_euler2d_x_tma(const CUtensorMap &map, const SweepArgs &a,
+                                                  cudaStream_t s)
+{
+    return launch_sweep_tma<R, 0, X_TP, X_NL>(map, a, s);
+}
+
+template <int R> cudaError_t launch_euler2d_y_tma(const CUtensorMap &map, const SweepArgs &a,
+                                                  cudaStream_t s)
+{
+    return launch_sweep_tma<R, 1, Y_TP, Y_NL>(map, a, s);
+}
+
+template cudaError_t launch_euler2d_x_tma<ENOMR_R>(const CUtensorMap &, const SweepArgs &,
+                                                   cudaStream_t);
+template cudaError_t launch_euler2d_y_tma<ENOMR_R>(const CUtensorMap &, const SweepArgs &,
                                                    cudaStream_t);
 
 }  // namespace enomr

@@ -20,11 +20,6 @@
 
 namespace enomr {
 
-// Tile shapes of the sweeps (interfaces per line x lines per CTA).
-constexpr int E1_TP = 64;
-constexpr int X_TP = 128, X_NL = 2;
-constexpr int Y_TP = 64, Y_NL = 4;
-
 // ---------------------------------------------------------------------------
 // Euler line sweep.  DIR 0: lines are rows (x contiguous); DIR 1: lines are
 // columns.  C = 3 (1D) or 4 (2D, components rho, m_x, m_y, E).
@@ -51,6 +46,29 @@ struct SweepSmem {
     static_assert(sizeof(unsigned short) * NL * S <= sizeof(double) * C * NL * TP &&
                       sizeof(unsigned short) * NL * S <= sizeof(int) * TP * NL,
                   "staging arrays must fit in the storage they share");
+};
+
+// View of a tile's shared memory used by sweep_tile and interface_flux.
+// U(q, line, s): state component q (line order: rho, m_n, [m_t], E) of
+// staged cell s of tile line `line`; F: its normal flux; P: sqrt(rho), u_n,
+// u_t, H; Fh(q, line, p): flux of interface p.  kLoads: the staging phase
+// loads the cells from global memory itself (true here); a view whose
+// cells are already in shared memory (the TMA ring of enomr_tma.cuh) reads
+// them in place.
+template <int R, int C, int DIR, int TP, int NL>
+struct ClassicTile {
+    static constexpr bool kLoads = true;
+    SweepSmem<R, C, TP, NL> &sm;
+    __device__ __forceinline__ double &U(int q, int line, int s) const { return sm.sU[q][line][s]; }
+    __device__ __forceinline__ double &F(int q, int line, int s) const { return sm.sF[q][line][s]; }
+    __device__ __forceinline__ double &P(int q, int line, int s) const { return sm.sP[q][line][s]; }
+    __device__ __forceinline__ double &Fh(int q, int line, int p) const { return sm.sFh[q][line][p]; }
+    __device__ __forceinline__ unsigned short *rep() const { return sm.rep; }
+    __device__ __forceinline__ unsigned short *slist() const { return sm.slist; }
+    __device__ __forceinline__ int *list() const { return sm.list; }
+    __device__ __forceinline__ int &nlist() const { return sm.nlist; }
+    __device__ __forceinline__ int &nrep() const { return sm.nrep; }
+    __device__ __forceinline__ unsigned long long (*red() const)[3] { return sm.red; }
 };
 
 // State of ghost cell craw (< 0 or >= the line length) of line L, in
@@ -94,21 +112,17 @@ __device__ __forceinline__ void side_cell(const SweepArgs &A, long long craw, lo
 }
 
 // Flux of interface x_{k-1/2}, k = x0 + p, of tile line `line` into
-// sm.sFh[.][line][p] (and the selections / field values when requested).
+// t.Fh(., line, p) (and the selections / field values when requested).
 // FLATP: the interface is flat (both sides' centre triples of cell states
 // are bitwise equal), e2: its two centre states are bitwise equal.  The
 // long path (FLATP false) holds warp votes: all 32 lanes of the warp call
 // it together, lanes with valid == false only vote.
-template <int R, int C, int DIR, int TP, int NL, bool FLATP>
+template <int R, int C, int DIR, int TP, int NL, bool FLATP, class Tile>
 __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0, long long l0,
-                                               const double *sA, SweepSmem<R, C, TP, NL> &sm,
-                                               int p, int line, bool valid, bool e2)
+                                               const double *sA, const Tile &t, int p, int line,
+                                               bool valid, bool e2)
 {
     constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
-    auto &sU = sm.sU;
-    auto &sF = sm.sF;
-    auto &sP = sm.sP;
-    auto &sFh = sm.sFh;
     const long long nlen = (DIR == 0) ? A.nx : A.ny;
     if constexpr (FLATP) {
         if (e2 && !A.ft_out) {
@@ -132,7 +146,7 @@ __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0,
             }
             const int sr = p + g;
 #pragma unroll
-            for (int q = 0; q < C; ++q) sFh[q][line][p] = sF[q][line][sr];
+            for (int q = 0; q < C; ++q) t.Fh(q, line, p) = t.F(q, line, sr);
             return;
         }
     }
@@ -145,10 +159,10 @@ __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0,
     bool eqLR = true;
 #pragma unroll
     for (int q = 0; q < C; ++q)
-        eqLR = eqLR && (__double_as_longlong(sU[q][line][sl]) == __double_as_longlong(sU[q][line][sr]));
-    const RoeFace rf = roe_face(eqLR, sP[0][line][sl], sP[1][line][sl], sP[2][line][sl],
-                                sP[3][line][sl], sP[0][line][sr], sP[1][line][sr],
-                                sP[2][line][sr], sP[3][line][sr], C == 4, A.gm1, A.inv_gm1);
+        eqLR = eqLR && (__double_as_longlong(t.U(q, line, sl)) == __double_as_longlong(t.U(q, line, sr)));
+    const RoeFace rf = roe_face(eqLR, t.P(0, line, sl), t.P(1, line, sl), t.P(2, line, sl),
+                                t.P(3, line, sl), t.P(0, line, sr), t.P(1, line, sr),
+                                t.P(2, line, sr), t.P(3, line, sr), C == 4, A.gm1, A.inv_gm1);
     if (valid && !positive(rf.c2)) atomicOr(A.status, ST_NONPHYS_ROE);
     const double uh = rf.uh, vh = rf.vh, Hh = rf.Hh, hq = rf.hq, cs = rf.cs, kap = rf.kap,
                  c2g = rf.c2g, b1 = rf.b1;
@@ -189,19 +203,19 @@ __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0,
     // w = l U and q = l F of staged cell s (the same operations on every path).
     auto project = [&](int f, int s, double l0c, double l1c, double &w, double &q) {
         if (C == 4 && f == 2) {
-            w = fma(l0c, sU[0][line][s], sU[2][line][s]);
-            q = fma(l0c, sF[0][line][s], sF[2][line][s]);
+            w = fma(l0c, t.U(0, line, s), t.U(2, line, s));
+            q = fma(l0c, t.F(0, line, s), t.F(2, line, s));
         } else {
-            w = sU[C - 1][line][s];
-            q = sF[C - 1][line][s];
+            w = t.U(C - 1, line, s);
+            q = t.F(C - 1, line, s);
             if (C == 4) {
-                w = fma(-vh, sU[2][line][s], w);
-                q = fma(-vh, sF[2][line][s], q);
+                w = fma(-vh, t.U(2, line, s), w);
+                q = fma(-vh, t.F(2, line, s), q);
             }
-            w = fma(l1c, sU[1][line][s], w);
-            q = fma(l1c, sF[1][line][s], q);
-            w = fma(l0c, sU[0][line][s], w);
-            q = fma(l0c, sF[0][line][s], q);
+            w = fma(l1c, t.U(1, line, s), w);
+            q = fma(l1c, t.F(1, line, s), q);
+            w = fma(l0c, t.U(0, line, s), w);
+            q = fma(l0c, t.F(0, line, s), q);
         }
     };
     auto accumulate = [&](int f, double ft) {
@@ -273,34 +287,29 @@ __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0,
     // over the owner's slot
     if (valid)
 #pragma unroll
-        for (int q = 0; q < C; ++q) sFh[q][line][p] = Fh[q];
+        for (int q = 0; q < C; ++q) t.Fh(q, line, p) = Fh[q];
 }
 
 // One tile: NL lines x TP interfaces starting at interface x0 of line l0.
 // All threads of the CTA must call it; it ends after its epilogue.
 // EXT: the 2D sweep with boundary sides and a body force (SweepArgs'
 // side_lo, side_hi, ..., src set); the plain instances leave them unread.
-template <int R, int C, int DIR, int TP, int NL, bool EXT = false>
+template <int R, int C, int DIR, int TP, int NL, bool EXT = false, class Tile>
 __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, long long l0,
-                                           const double *sA, SweepSmem<R, C, TP, NL> &sm)
+                                           const double *sA, const Tile &t)
 {
     constexpr int g = (R + 1) / 2, S = TP + 2 * g - 1;
     constexpr int NT = TP * NL;
     constexpr int QN = (DIR == 0) ? 1 : 2;  // normal momentum component
     constexpr int QT = (DIR == 0) ? 2 : 1;  // tangential momentum component (C = 4)
-    auto &sU = sm.sU;
-    auto &sF = sm.sF;
-    auto &sP = sm.sP;
-    auto &sFh = sm.sFh;
-
     const long long nx = A.nx, ny = A.ny, ncell = nx * ny;
     const long long nlen = (DIR == 0) ? nx : ny;
     const long long nlines = (DIR == 0) ? ny : nx;
     const int tid = threadIdx.x;
 
     if (tid == 0) {
-        sm.nlist = 0;
-        sm.nrep = 0;
+        t.nlist() = 0;
+        t.nrep() = 0;
     }
     __syncthreads();
     // ---- stage cells, primitives and physical fluxes (normal direction).
@@ -334,7 +343,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
         double u[C];
 #pragma unroll
         for (int q = 0; q < C; ++q) u[q] = 0.0;
-        if (act) {
+        if (!Tile::kLoads) {
+            // cells already staged (and their ghosts filled) in shared memory
+            if (act)
+#pragma unroll
+                for (int q = 0; q < C; ++q) u[q] = t.U(q, line, s);
+        } else if (act) {
             long long L = l0 + line;
             if (L >= nlines) L = nlines - 1;
             const long long craw = x0 - g + s;
@@ -346,10 +360,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
 #pragma unroll
                 for (int q = 0; q < C; ++q) u[q] = A.U[q * ncell + gi];
             }
-            sU[0][line][s] = u[0];
-            sU[1][line][s] = u[QN];
-            if (C == 4) sU[2][line][s] = u[QT];
-            sU[C - 1][line][s] = u[C - 1];
+            t.U(0, line, s) = u[0];
+            t.U(1, line, s) = u[QN];
+            if (C == 4) t.U(2, line, s) = u[QT];
+            t.U(C - 1, line, s) = u[C - 1];
         }
         bool same = lane >= PD && s > 0;
 #pragma unroll
@@ -363,21 +377,21 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
         // below this one on the same line (a line's first lane is one)
         unsigned m = reps & (lane == 31 ? FULL : ((2u << lane) - 1u));
         if (DIR == 1) m &= CLS << (lane % NL);
-        if (act) sm.rep[idx] = (unsigned short)(base + 31 - __clz(m));
+        if (act) t.rep()[idx] = (unsigned short)(base + 31 - __clz(m));
         if (reps) {
             int b0 = 0;
-            if (lane == 0) b0 = atomicAdd(&sm.nrep, __popc(reps));
+            if (lane == 0) b0 = atomicAdd(&t.nrep(), __popc(reps));
             b0 = __shfl_sync(FULL, b0, 0);
-            if (rep) sm.slist[b0 + __popc(reps & ((1u << lane) - 1u))] = (unsigned short)idx;
+            if (rep) t.slist()[b0 + __popc(reps & ((1u << lane) - 1u))] = (unsigned short)idx;
         }
     }
     __syncthreads();
     {
-        const int nrep = sm.nrep;
+        const int nrep = t.nrep();
         for (int b = tid & ~31; b < nrep; b += NT) {
-            const int t = b + lane;
-            if (t < nrep) {
-                const int idx = sm.slist[t];
+            const int j = b + lane;
+            if (j < nrep) {
+                const int idx = t.slist()[j];
                 int line, s;
                 if (DIR == 0) {
                     line = idx / S;
@@ -386,23 +400,23 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
                     s = idx / NL;
                     line = idx - s * NL;
                 }
-                const double u0 = sU[0][line][s], uE = sU[C - 1][line][s];
-                const StagedCell<C> sc_ = stage_cell<C>(u0, sU[1][line][s],
-                                                        (C == 4) ? sU[2][line][s] : 0.0, uE, A.gm1);
+                const double u0 = t.U(0, line, s), uE = t.U(C - 1, line, s);
+                const StagedCell<C> sc_ = stage_cell<C>(u0, t.U(1, line, s),
+                                                        (C == 4) ? t.U(2, line, s) : 0.0, uE, A.gm1);
                 if (!positive(u0) || !positive(sc_.p) || !below_1e300(uE))
                     atomicOr(A.status, ST_NONPHYS_CELL);
 #pragma unroll
-                for (int q = 0; q < C; ++q) sF[q][line][s] = sc_.F[q];
-                sP[0][line][s] = sc_.sq;
-                sP[1][line][s] = sc_.un;
-                sP[2][line][s] = sc_.ut;
-                sP[3][line][s] = sc_.H;
+                for (int q = 0; q < C; ++q) t.F(q, line, s) = sc_.F[q];
+                t.P(0, line, s) = sc_.sq;
+                t.P(1, line, s) = sc_.un;
+                t.P(2, line, s) = sc_.ut;
+                t.P(3, line, s) = sc_.H;
             }
         }
     }
     __syncthreads();
     for (int idx = tid; idx < NS; idx += NT) {
-        const int r = sm.rep[idx];
+        const int r = t.rep()[idx];
         if (r != idx) {
             int line, s, lr, sr_;
             if (DIR == 0) {
@@ -417,9 +431,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
                 lr = r - sr_ * NL;
             }
 #pragma unroll
-            for (int q = 0; q < C; ++q) sF[q][line][s] = sF[q][lr][sr_];
+            for (int q = 0; q < C; ++q) t.F(q, line, s) = t.F(q, lr, sr_);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) sP[q][line][s] = sP[q][lr][sr_];
+            for (int q = 0; q < 4; ++q) t.P(q, line, s) = t.P(q, lr, sr_);
         }
     }
     __syncthreads();
@@ -449,7 +463,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
             bool e = true;
 #pragma unroll
             for (int q = 0; q < C; ++q)
-                e = e && (__double_as_longlong(sU[q][line][a]) == __double_as_longlong(sU[q][line][b]));
+                e = e && (__double_as_longlong(t.U(q, line, a)) == __double_as_longlong(t.U(q, line, b)));
             return e;
         };
         const bool e0 = same(sl - 2, sl - 1), e1 = same(sl - 1, sl), e2 = same(sl, sr),
@@ -458,24 +472,24 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
         const bool minus_flat = (e3 && e4) || (e1 && e2);  // centre cell k (mirrored)
         const bool flat = plus_flat && minus_flat;
         if (valid && flat)
-            interface_flux<R, C, DIR, TP, NL, true>(A, x0, l0, sA, sm, p, line, true, e2);
+            interface_flux<R, C, DIR, TP, NL, true>(A, x0, l0, sA, t, p, line, true, e2);
         // append the other valid interfaces, in lane order within each warp
         const unsigned need = __ballot_sync(FULL, valid && !flat);
         if (need) {
             int base = 0;
-            if (lane == 0) base = atomicAdd(&sm.nlist, __popc(need));
+            if (lane == 0) base = atomicAdd(&t.nlist(), __popc(need));
             base = __shfl_sync(FULL, base, 0);
-            if ((need >> lane) & 1u) sm.list[base + __popc(need & ((1u << lane) - 1u))] = line * TP + p;
+            if ((need >> lane) & 1u) t.list()[base + __popc(need & ((1u << lane) - 1u))] = line * TP + p;
         }
     }
     __syncthreads();
     {
-        const int n = sm.nlist;
+        const int n = t.nlist();
         for (int base = tid & ~31; base < n; base += NT) {
-            const int t = base + (tid & 31);
-            const bool act = t < n;
-            const int e = sm.list[act ? t : base];
-            interface_flux<R, C, DIR, TP, NL, false>(A, x0, l0, sA, sm, e % TP, e / TP, act, false);
+            const int j = base + (tid & 31);
+            const bool act = j < n;
+            const int e = t.list()[act ? j : base];
+            interface_flux<R, C, DIR, TP, NL, false>(A, x0, l0, sA, t, e % TP, e / TP, act, false);
         }
     }
     __syncthreads();
@@ -496,20 +510,20 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
             for (int q = 0; q < C; ++q) {
                 // map line component back to the state component
                 const int qs = (q == 1) ? QN : ((C == 4 && q == 2) ? QT : q);
-                const double D = -(sFh[q][line][p + 1] - sFh[q][line][p]) * A.inv_h;
+                const double D = -(t.Fh(q, line, p + 1) - t.Fh(q, line, p)) * A.inv_h;
                 if constexpr (EXT) {
                     // body force (0, rho g_n, rho g_t, m_n g_n + m_t g_t)
                     double S = 0.0;
-                    const double rho = sU[0][line][sc];
+                    const double rho = t.U(0, line, sc);
                     if (q == 1) S = __dmul_rn(rho, A.g_n);
                     if (C == 4 && q == 2) S = __dmul_rn(rho, A.g_t);
                     if (q == C - 1)
-                        S = (C == 4) ? __dadd_rn(__dmul_rn(sU[1][line][sc], A.g_n),
-                                                 __dmul_rn(sU[2][line][sc], A.g_t))
-                                     : __dmul_rn(sU[1][line][sc], A.g_n);
-                    o[q] = epilogue(A.epi, qs * ncell + gi, D, sU[q][line][sc], A.src != 0, S);
+                        S = (C == 4) ? __dadd_rn(__dmul_rn(t.U(1, line, sc), A.g_n),
+                                                 __dmul_rn(t.U(2, line, sc), A.g_t))
+                                     : __dmul_rn(t.U(1, line, sc), A.g_n);
+                    o[q] = epilogue(A.epi, qs * ncell + gi, D, t.U(q, line, sc), A.src != 0, S);
                 } else {
-                    o[q] = epilogue(A.epi, qs * ncell + gi, D, sU[q][line][sc]);
+                    o[q] = epilogue(A.epi, qs * ncell + gi, D, t.U(q, line, sc));
                 }
             }
             if (C == 3 && A.alpha_next) {
@@ -531,11 +545,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
             }
         }
         if ((tid & 31) == 0)
-            for (int k3 = 0; k3 < 3; ++k3) sm.red[tid >> 5][k3] = ws[k3];
+            for (int k3 = 0; k3 < 3; ++k3) t.red()[tid >> 5][k3] = ws[k3];
         __syncthreads();
         if (tid < 3) {
             unsigned long long m = 0;
-            for (int wi = 0; wi < NT / 32; ++wi) m = m > sm.red[wi][tid] ? m : sm.red[wi][tid];
+            for (int wi = 0; wi < NT / 32; ++wi) m = m > t.red()[wi][tid] ? m : t.red()[wi][tid];
             atomicMax((unsigned long long *)(A.alpha_next + tid), m);
         }
     }
@@ -560,7 +574,7 @@ __global__ void __launch_bounds__(TP *NL, SWEEP_THREADS_PER_SM / (TP * NL)) k_sw
     load_a_table<R>(sA, threadIdx.x, TP * NL);
     const long long x0 = (long long)((DIR == 0) ? blockIdx.x : blockIdx.y) * (TP - 1);
     const long long l0 = (long long)((DIR == 0) ? blockIdx.y : blockIdx.x) * NL;
-    sweep_tile<R, C, DIR, TP, NL, EXT>(A, x0, l0, sA, sm);
+    sweep_tile<R, C, DIR, TP, NL, EXT>(A, x0, l0, sA, ClassicTile<R, C, DIR, TP, NL>{sm});
 }
 
 // ---------------------------------------------------------------------------
@@ -602,7 +616,7 @@ __global__ void __launch_bounds__(TP) k_batch_stage(BatchArgs B)
         A.epi.Un = B.Un + base;
         A.epi.Dprev = nullptr;
         A.epi.out = B.out + base;
-        sweep_tile<R, 3, 0, TP, 1>(A, tl.x0, 0, sA, sm);
+        sweep_tile<R, 3, 0, TP, 1>(A, tl.x0, 0, sA, ClassicTile<R, 3, 0, TP, 1>{sm});
     }
 }
 

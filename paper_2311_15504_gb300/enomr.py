@@ -26,6 +26,8 @@ class _Side(ctypes.Structure):
                 ("state_lo", ctypes.c_double * 4), ("state_hi", ctypes.c_double * 4)]
 PERIODIC, TRANSMISSIVE = 0, 1
 ORDERS = (5, 7, 9, 11, 13, 15, 17)
+# staging of the 2D sweeps' tiles (enomr_set_staging)
+STAGING_AUTO, STAGING_LOADS, STAGING_TMA = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libenomr.so")
@@ -68,6 +70,7 @@ _SIGS = {
     "enomr_set_body_force": (_I, [_P, _D, _D]),
     "enomr_set_time": (_I, [_P, _D]),
     "enomr_get_time": (_I, [_P, ctypes.POINTER(_D)]),
+    "enomr_set_staging": (_I, [_P, _I]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -263,6 +266,11 @@ class Solver:
         """Four sides as (kind_lo, state_lo, kind_hi, state_hi, split0, rate)."""
         for i, sd in enumerate(sides):
             self.set_side(i, sd[0], sd[1], sd[2], sd[3], sd[4], sd[5])
+
+    def set_staging(self, mode):
+        """STAGING_AUTO (TMA where the state allows it), STAGING_LOADS or
+        STAGING_TMA (TMA only; other states raise)."""
+        _check(_lib.enomr_set_staging(self._ctx, int(mode)), "enomr_set_staging")
 
     def set_body_force(self, gx, gy):
         _check(_lib.enomr_set_body_force(self._ctx, float(gx), float(gy)),
