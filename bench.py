@@ -64,16 +64,22 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, period_ms=50):
         self.gpu = gpu_index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
+        self.marks = {}
+
+    def mark(self, name):
+        """Remember the current sample count (start or end of a window)."""
+        self.marks[name] = len(self.lines)
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -92,9 +98,16 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        return self.summary()
+
+    def summary(self, start=None, end=None):
+        """Median SM clock, max clock and throttle reasons of the samples
+        between two marks (default: all samples)."""
+        lo = self.marks.get(start, 0) if start else 0
+        hi = self.marks.get(end, len(self.lines)) if end else len(self.lines)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[lo:hi]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -108,7 +121,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "period_ms": self.period_ms}
 
 
 # ---------------------------------------------------------------------------
@@ -205,7 +219,8 @@ def flat_interfaces(U, axis):
             distinct)
 
 
-KERNEL_SOURCES = ("enomr_sweep.cuh", "enomr_kernels.cuh", "enomr_common.cuh", "gen_coeffs.py")
+KERNEL_SOURCES = ("enomr_sweep.cuh", "enomr_tma.cuh", "enomr_kernels.cuh", "enomr_common.cuh",
+                  "gen_coeffs.py")
 
 
 def kernel_source_digest():
@@ -287,6 +302,23 @@ def batched_gain(enomr, workloads, dev, a, nprob=4096, order=9, reps=5):
         for sp, v in zip(singles, views):
             sp.step(v, 0.0, a.cfl)
     ms_p = timed(gp)
+    # the fair per-problem baseline: the same launches spread over 8 streams,
+    # captured as 8 parallel branches of one graph (independent problems,
+    # each with its own context)
+    nbr = 8
+    branches = [torch.cuda.Stream(device=dev) for _ in range(nbr)]
+    gc = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gc):
+        cap = torch.cuda.current_stream(dev)
+        for b in branches:
+            b.wait_stream(cap)
+        for k, b in enumerate(branches):
+            with torch.cuda.stream(b):
+                for p_ in range(k, nprob, nbr):
+                    singles[p_].step(views[p_], 0.0, a.cfl)
+        for b in branches:
+            cap.wait_stream(b)
+    ms_c = timed(gc)
     # same arithmetic: after the same number of steps the two states agree bitwise
     Ub2, Up2 = B.pack(Us), B.pack(Us)
     with torch.cuda.stream(side):
@@ -303,72 +335,139 @@ def batched_gain(enomr, workloads, dev, a, nprob=4096, order=9, reps=5):
                         f"({cells} cells), order {order}, transmissive, CFL {a.cfl}",
             "batched": {"value": cells * 3 / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
                         "tile": tile, "grid": grid, "launches_per_step": 5},
-            "per_problem": {"value": cells * 3 / (ms_p * 1e-3), "unit": UNIT,
-                            "ms_per_step": ms_p, "launches_per_step": 7 * nprob},
-            "gain": ms_p / ms_b, "bitwise_identical_after_2_steps": identical}
+            "per_problem_serial": {"value": cells * 3 / (ms_p * 1e-3), "unit": UNIT,
+                                   "ms_per_step": ms_p, "launches_per_step": 7 * nprob,
+                                   "form": "one stream, one CUDA graph"},
+            "per_problem_concurrent": {"value": cells * 3 / (ms_c * 1e-3), "unit": UNIT,
+                                       "ms_per_step": ms_c, "launches_per_step": 7 * nprob,
+                                       "form": f"{nbr} parallel branches of one CUDA graph"},
+            "gain": ms_c / ms_b, "gain_vs_serial": ms_p / ms_b,
+            "gain_definition": "concurrent per-problem launches / persistent batched step",
+            "bitwise_identical_after_2_steps": identical}
 
 
-def adjoint_ratio(enomr, workloads, dev, n=1024, order=9, steps=10, cfl=0.5):
-    """Isentropic vortex (periodic, order 9): time of one SSP-RK3 step
-    against one step of the adjoint (stage recomputation from the step's
-    checkpoint, three RHS transposes, the RK transpose)."""
+def adjoint_ratio(enomr, workloads, dev, n=1024, order=9, steps=200, cfl=0.5):
+    """The adjoint workload: isentropic vortex n^2 (periodic, order 9),
+    `steps` CFL steps through the differentiable rollout (per-step
+    checkpoints; dt kept on the device and recomputed from each checkpoint
+    in the backward pass), loss 1/2 ||rho(t) - rho_target||^2.  Times the
+    forward rollout (steps + checkpoint copies) and the backward pass; the
+    device memory in use at the peak (all checkpoints alive) is read from
+    the driver, so the library's own scratch is included."""
     import torch
     U0, h, _ = workloads.isentropic_vortex(n)
+    rng = np.random.Generator(np.random.PCG64(2024))
+    Ut = U0.copy()
+    Ut[0] += 1e-3 * rng.standard_normal((n, n))
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info(dev)
     s = enomr.Solver(enomr.EULER, (n, n), order=order, dx=h, dy=h, bc=enomr.PERIODIC,
                      device=dev)
-    U = torch.from_numpy(U0).to(dev)
-    dt = s.cfl_dt(U, 0.5)
-    ck = [U.clone() for _ in range(steps)]
-    g = torch.randn_like(U)
-    out = torch.empty_like(U)
-    s.step(U, dt=dt)
-    s.step_vjp(ck[0], dt, g, out=out)
+    tgt_state = torch.from_numpy(Ut).to(dev)
+    for _ in range(steps):
+        s.step(tgt_state, 0.0, cfl)
+    tgt = tgt_state[0].clone()
+    del tgt_state
+    # warm-up of both directions
+    x = torch.from_numpy(U0).to(dev).requires_grad_(True)
+    out = enomr.rollout(x, s, 2, cfl=cfl)
+    (0.5 * ((out[0] - tgt) ** 2).sum()).backward()
     torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    x = torch.from_numpy(U0).to(dev).requires_grad_(True)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     e[0].record()
-    for i in range(steps):
-        ck[i].copy_(U)
-        s.step(U, dt=dt)
+    out = enomr.rollout(x, s, steps, cfl=cfl)
+    loss = 0.5 * ((out[0] - tgt) ** 2).sum()
     e[1].record()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    loss.backward()
     e[2].record()
-    for i in reversed(range(steps)):
-        s.step_vjp(ck[i], dt, g, out=out)
-        g, out = out, g
-    e[3].record()
     torch.cuda.synchronize()
     fwd = e[0].elapsed_time(e[1]) / steps
-    bwd = e[2].elapsed_time(e[3]) / steps
+    bwd = e[1].elapsed_time(e[2]) / steps
+    g_norm = float(x.grad.norm())
     s.close()
-    return {"workload": f"isentropic vortex {n}^2 periodic, order {order}, fixed dt",
-            "forward_ms_per_step": fwd, "adjoint_ms_per_step": bwd, "ratio": bwd / fwd,
-            "forward_includes_checkpoint_copy": True}
+    return {"workload": f"isentropic vortex {n}^2 periodic, order {order}, {steps} CFL steps, "
+                        "loss 1/2 ||rho(t) - rho_target||^2",
+            "forward_ms_per_step": round(fwd, 4), "adjoint_ms_per_step": round(bwd, 4),
+            "ratio": bwd / fwd, "forward_includes_checkpoint_copy": True,
+            "device_bytes_at_peak": int(free0 - free1),
+            "checkpoint_bytes": int(steps * U0.nbytes),
+            "host_syncs_per_step": 0, "grad_norm": g_norm}
 
 
-def sweep_fracs(enomr, solver, U, order, n, cfl, peak_ops, steps=2):
-    """FP64-operation roofline fractions of the x and y sweeps of `steps`
-    SSP-RK3 steps from state U (each sweep timed live on the library's
-    stream; work from the selections and flat-interface counts of U), and
-    their compulsory bytes against the measured HBM bandwidth."""
+def probe_ops_peak(enomr, dev):
+    """Measured FP64 throughput: the all-SM FMA-chain probe, in flop/s and
+    in FP64 pipe operations/s (an fma is one operation, two flops)."""
+    fl, _ = enomr.probe_fp64_fma(iters=20000, device=dev)
+    return fl, fl / 2.0
+
+
+def sweep_fracs(enomr, solver, U, order, n, cfl, peak_ops, steps=2, probe_ops=None):
+    """The x and y sweeps of `steps` SSP-RK3 steps from state U, each timed
+    live on the library's stream (mean ms per launch), against:
+      frac (= frac_executed): the executed-work model (sweep_work with the
+        state's flat-interface and distinct-cell counts) over the unit-count
+        FP64 peak;
+      frac_method: the method's per-interface work with every interface and
+        every cell evaluated in full (no flat-interface or repeated-cell
+        shortcut) over the same peak -- above 1 where the shortcuts skip
+        most of the work;
+      *_probe: the executed work over the measured FMA-probe rate;
+      *_hbm_frac: the compulsory bytes over the measured copy bandwidth.
+    Work from the selections and flat-interface counts of U."""
     import torch
     T = enomr.num_tested(order)
     nsx = 8 * n * (n + 1)
     sel = solver.selection(U)
     hx = torch.bincount(sel[:nsx].long(), minlength=T + 3).cpu().numpy()
     hy = torch.bincount(sel[nsx:].long(), minlength=T + 3).cpu().numpy()
-    wx = sweep_work(order, 4, hx, n * (n + 1), flat_interfaces(U, 0))
-    wy = sweep_work(order, 4, hy, n * (n + 1), flat_interfaces(U, 1), stage_epilogue=True)
+    nint = n * (n + 1)
+    work = {"x": (sweep_work(order, 4, hx, nint, flat_interfaces(U, 0)),
+                  sweep_work(order, 4, hx, nint, (0, 0, 0, n * n))),
+            "y": (sweep_work(order, 4, hy, nint, flat_interfaces(U, 1), stage_epilogue=True),
+                  sweep_work(order, 4, hy, nint, (0, 0, 0, n * n), stage_epilogue=True))}
     out = {}
-    for kind, w in ((1, wx), (2, wy)):
+    for kind, key in ((1, "x"), (2, "y")):
         Uc = U.clone()
         solver.profile_begin(kind, 3 * steps)
         for _ in range(steps):
             solver.step(Uc, 0.0, cfl)
         nl, ms = solver.profile_end()
-        key = "x" if kind == 1 else "y"
-        out[key] = round(w[1] / (ms / max(nl, 1) * 1e-3) / peak_ops, 4)
+        avg = ms / max(nl, 1)
+        (fl, ops), (mfl, mops) = work[key]
+        out[key] = round(ops / (avg * 1e-3) / peak_ops, 4)
+        out[key + "_ms"] = round(avg, 4)
+        out[key + "_method"] = round(mops / (avg * 1e-3) / peak_ops, 4)
+        if probe_ops:
+            out[key + "_probe"] = round(ops / (avg * 1e-3) / probe_ops, 4)
         if ms > 0:  # the same launches against the measured copy bandwidth
-            out[key + "_hbm_frac"] = hbm_side(n, kind - 1, ms / max(nl, 1))["frac"]
+            out[key + "_hbm_frac"] = hbm_side(n, kind - 1, avg)["frac"]
+        del Uc
     return out
+
+
+def scalar_work(order, sel, n, staged_ops):
+    """Executed FP64 operations of one scalar (advection or Burgers) launch
+    on n cells: per interface the staged split value (staged_ops), the
+    baseline indicator (6), the indicators of the tested candidates up to
+    the chosen one (|S| each), the reconstruction (2g-1 for a tested
+    stencil, 1 for minmod), the flux difference (2) and the stage update
+    (4); only the window that carries the flux (f^+ for a > 0, u > 0) is
+    evaluated.  sel: histogram of that side's selections."""
+    import oracle  # table sizes only
+    g = (order + 1) // 2
+    T = oracle.num_tested(order)
+    sizes = np.array([oracle.candidate(order, t)[0] + oracle.candidate(order, t)[1] + 1
+                      for t in range(T)], dtype=np.float64)
+    cum = np.cumsum(sizes)
+    cnt = np.asarray(sel, dtype=np.float64)
+    w = float(n + 1) * (staged_ops + 6) + float(n) * (2 + 4)
+    for t in range(T):
+        w += cnt[t] * (cum[t] + (2 * g - 1))
+    w += (cnt[T] + cnt[T + 1]) * (cum[-1] + 1) + cnt[T + 2] * 1
+    return w
 
 
 def paper_run(enomr, dev, name, U0, dx, dy, order, sides, gravity, gamma, cfl, t_end):
@@ -547,6 +646,183 @@ def vortex_rate(enomr, workloads, dev, a):
             "ms_per_step": f0.elapsed_time(f1) / a.steps}
 
 
+def timed_steps(solver, U, steps, dt=0.0, cfl=0.5):
+    """ms of `steps` steps of solver on U (CUDA events on the current stream)."""
+    import torch
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(steps):
+        solver.step(U, dt, cfl)
+    f1.record()
+    torch.cuda.synchronize()
+    return f0.elapsed_time(f1)
+
+
+def rate_of(solver, Ustate, steps=2, dt=0.0, cfl=0.5):
+    """cell-updates/s per RK stage of `steps` steps after one warm-up step."""
+    import torch
+    solver.step(Ustate, dt, cfl)
+    torch.cuda.synchronize()
+    ms = timed_steps(solver, Ustate, steps, dt, cfl)
+    cells = Ustate[0].numel() if Ustate.dim() > 1 else Ustate.numel()
+    return cells * 3 * steps / (ms * 1e-3)
+
+
+def small_configs(enomr, workloads, dev):
+    """The paper-sized 1D runs, which are latency-bound: advection N = 200
+    (orders 5, 7, 9, the sine and the unit step, CFL 0.5) and the
+    shock/entropy-wave interaction at N = 400, 1600, 6400 (orders 5, 9, 13,
+    17, CFL steps on the device).  Each: microseconds per SSP-RK3 step and
+    cell-updates/s per RK stage, from a plain stream of 200 steps and from a
+    CUDA graph of 50 steps replayed 4 times (launch overhead removed)."""
+    import torch
+
+    def measure(solver, U, dt):
+        for _ in range(3):
+            solver.step(U, dt, 0.5)
+        torch.cuda.synchronize()
+        ms_stream = timed_steps(solver, U, 200, dt) / 200
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            solver.step(U, dt, 0.5)
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            for _ in range(50):
+                solver.step(U, dt, 0.5)
+        gr.replay()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for _ in range(4):
+            gr.replay()
+        f1.record()
+        torch.cuda.synchronize()
+        ms_graph = f0.elapsed_time(f1) / 200
+        cells = U.shape[-1]
+        return {"us_per_step_stream": round(ms_stream * 1e3, 2),
+                "us_per_step_graph": round(ms_graph * 1e3, 2),
+                "value_graph": cells * 3 / (ms_graph * 1e-3)}
+
+    out = {"config1_advection_200": {}, "config2_shock_entropy": {}, "unit": UNIT}
+    for R in (5, 7, 9):
+        for kind in ("sine", "step"):
+            u, h = (workloads.advection_sine(200) if kind == "sine"
+                    else workloads.advection_step(200))
+            sa = enomr.Solver(enomr.ADVECTION, 200, order=R, dx=h, bc=enomr.PERIODIC, device=dev)
+            out["config1_advection_200"][f"R{R}_{kind}"] = measure(
+                sa, torch.from_numpy(u).to(dev), 0.5 * h)
+            sa.close()
+    for N in (400, 1600, 6400):
+        for R in (5, 9, 13, 17):
+            U, h = workloads.shock_entropy(N)
+            se = enomr.Solver(enomr.EULER, N, order=R, dx=h, bc=enomr.TRANSMISSIVE, device=dev)
+            out["config2_shock_entropy"][f"N{N}_R{R}"] = measure(se, torch.from_numpy(U).to(dev),
+                                                                 0.0)
+            se.close()
+    return out
+
+
+def scalar_fracs(enomr, workloads, dev, peak_ops, hbm_peak):
+    """Scalar advection (sin(pi x)) and Burgers (1 + 0.5 sin^3(pi x)) at
+    N = 2^24, orders 5, 9, 17: rate, the kernel's mean launch time, its
+    executed FP64 work (scalar_work) over the unit-count peak, and its
+    compulsory bytes (read U^(s) and U^n, write the stage: 24 B per cell)
+    over the measured copy bandwidth."""
+    import torch
+    N = 1 << 24
+    out = {}
+    for name, eq, make, staged in (("advection_2p24", enomr.ADVECTION, workloads.advection_sine, 1),
+                                   ("burgers_2p24", enomr.BURGERS, workloads.burgers_sine3, 2)):
+        vals = {}
+        for R in (5, 9, 17):
+            u, h = make(N)
+            sv = enomr.Solver(eq, N, order=R, dx=h, bc=enomr.PERIODIC, device=dev)
+            ud = torch.from_numpy(u).to(dev)
+            dt = 0.5 * h if eq == enomr.ADVECTION else 0.0
+            rate = rate_of(sv, ud, steps=4, dt=dt)
+            sel = sv.selection(ud)
+            T = enomr.num_tested(R)
+            hist = torch.bincount(sel[:N + 1].long(), minlength=T + 3).cpu().numpy()
+            ops = scalar_work(R, hist, N, staged)
+            sv.profile_begin(1, 12)
+            timed_steps(sv, ud, 4, dt)
+            nl, ms = sv.profile_end()
+            avg = ms / max(nl, 1)
+            vals[str(R)] = {"value": rate, "kernel_ms": round(avg, 4),
+                            "fp64_op_frac": round(ops / (avg * 1e-3) / peak_ops, 4),
+                            "hbm_frac": (round(24.0 * N / (avg * 1e-3) / 1e9 / hbm_peak, 4)
+                                         if hbm_peak else None)}
+            sv.close()
+        out[name] = {"workload": f"{name.split('_')[0]}, N = 2^24, periodic, SSP-RK3",
+                     "unit": UNIT, "values": vals}
+    return out
+
+
+def per_order_vortex(enomr, workloads, dev, n, cfl, peak_ops, probe_ops):
+    """The long path at every order: the isentropic vortex (no flat windows)
+    on n^2, rate (1 warm-up + 2 timed steps) and both sweeps' fractions."""
+    import torch
+    Uv, hv, _ = workloads.isentropic_vortex(n)
+    out = {}
+    for R in enomr.ORDERS:
+        sv = enomr.Solver(enomr.EULER, (n, n), order=R, dx=hv, dy=hv, bc=enomr.PERIODIC,
+                          device=dev)
+        U = torch.from_numpy(Uv).to(dev)
+        out[str(R)] = {"value": rate_of(sv, U, cfl=cfl),
+                       **sweep_fracs(enomr, sv, U, R, n, cfl, peak_ops, probe_ops=probe_ops)}
+        sv.close()
+        del U
+    return {"workload": f"isentropic vortex {n}^2 periodic (every interface on the long path)",
+            "unit": UNIT, "orders": out}
+
+
+def riemann_sizes(enomr, workloads, dev, cfl, steps=20):
+    """The four-quadrant Riemann workload at 1024^2 and 2048^2 (orders 9
+    and 17): rate of `steps` CFL steps from t = 0 after one warm-up step."""
+    import torch
+    out = {}
+    for n in (1024, 2048):
+        U0, dx, dy = workloads.riemann2d(n, n, seed=0)
+        for R in (9, 17):
+            sk = enomr.Solver(enomr.EULER, (n, n), order=R, dx=dx, dy=dy,
+                              bc=enomr.TRANSMISSIVE, device=dev)
+            U = torch.from_numpy(U0).to(dev)
+            sk.step(U.clone(), 0.0, cfl)
+            ms = timed_steps(sk, U, steps, cfl=cfl)
+            out[f"{n}_R{R}"] = {"value": n * n * 3 * steps / (ms * 1e-3),
+                                "ms_per_step": round(ms / steps, 4)}
+            sk.close()
+    return {"unit": UNIT, "run": f"{steps} CFL steps from t = 0", "values": out}
+
+
+def staging_ab(enomr, s, U0, dev, steps, cfl):
+    """The same trajectory (`steps` CFL steps from t = 0) with the sweeps'
+    tiles staged by TMA and with plain loads: each sweep's mean launch time
+    and the step time.  Both give the same bits."""
+    import torch
+    out = {}
+    for name, mode in (("tma", enomr.STAGING_AUTO), ("loads", enomr.STAGING_LOADS)):
+        s.set_staging(mode)
+        r = {}
+        for kind, key in ((1, "x_ms"), (2, "y_ms")):
+            U = torch.from_numpy(U0).to(dev)
+            s.profile_begin(kind, 3 * steps)
+            for _ in range(steps):
+                s.step(U, 0.0, cfl)
+            nl, ms = s.profile_end()
+            r[key] = round(ms / max(nl, 1), 4)
+        U = torch.from_numpy(U0).to(dev)
+        r["step_ms"] = round(timed_steps(s, U, steps, cfl=cfl) / steps, 4)
+        out[name] = r
+    s.set_staging(enomr.STAGING_AUTO)
+    out["tma_speedup_step"] = round(out["loads"]["step_ms"] / out["tma"]["step_ms"], 4)
+    return out
+
+
 def main_ours(a):
     import torch
     import torch.distributed as dist
@@ -560,6 +836,8 @@ def main_ours(a):
     dev = torch.device("cuda", local)
     from paper_2311_15504_gb300 import enomr, workloads
 
+    clk = ClockSampler(local)
+    clk.start()
     n, R = a.n, a.order
     U0, dx, dy = workloads.riemann2d(n, n, seed=rank)
     s = enomr.Solver(enomr.EULER, (n, n), order=R, dx=dx, dy=dy, bc=enomr.TRANSMISSIVE,
@@ -571,18 +849,18 @@ def main_ours(a):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clk = ClockSampler(local)
-    clk.start()
     s.profile_begin(1, 3 * a.steps)  # x sweep: timed live during the run
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    clk.mark("timed_start")
     e0.record()
     for _ in range(a.steps):
         s.step(U, 0.0, a.cfl)
     e1.record()
     torch.cuda.synchronize()
-    clocks = clk.stop()
+    time.sleep(0.12)  # let the sampler take the region's last samples
+    clk.mark("timed_end")
     ms = e0.elapsed_time(e1)
     nx_launch, x_ms = s.profile_end()
     s.check_status()
@@ -591,8 +869,9 @@ def main_ours(a):
     launches_per_step = 1 + 3 + 2 * 3  # dt, 3 alpha reductions, 2 sweeps x 3 stages
 
     extras = {}
+    U_final = U
     if rank == 0 and not a.no_extras:
-        # y sweep, timed over the same number of steps right after the run
+        # y sweep and alpha, timed over the same trajectory right after the run
         Uy = torch.from_numpy(U0).to(dev)
         s.profile_begin(2, 3 * a.steps)
         for _ in range(a.steps):
@@ -603,6 +882,7 @@ def main_ours(a):
         for _ in range(a.steps):
             s.step(Uy, 0.0, a.cfl)
         na_launch, a_ms = s.profile_end()
+        del Uy
         # algorithmic work of a sweep: selection histograms and flat-interface
         # counts of the step states of the same trajectory (U^n of every
         # sampled step stands in for its three stage states), averaged
@@ -626,13 +906,17 @@ def main_ours(a):
             s.step(Us, 0.0, a.cfl)
         hx, hy, cx, cy = hx / ns, hy / ns, cx / ns, cy / ns
         del Us
-        wx = sweep_work(R, 4, hx, n * (n + 1), cx)
-        wy = sweep_work(R, 4, hy, n * (n + 1), cy, stage_epilogue=True)
-        extras["flat_interface_fraction"] = [cx[0] / (n * (n + 1)), cy[0] / (n * (n + 1))]
+        nint = n * (n + 1)
+        wx = sweep_work(R, 4, hx, nint, cx)
+        wy = sweep_work(R, 4, hy, nint, cy, stage_epilogue=True)
+        mx = sweep_work(R, 4, hx, nint, (0, 0, 0, n * n))
+        my = sweep_work(R, 4, hy, nint, (0, 0, 0, n * n), stage_epilogue=True)
+        extras["flat_interface_fraction"] = [cx[0] / nint, cy[0] / nint]
         extras["distinct_cell_fraction"] = [cx[3] / (n * n), cy[3] / (n * n)]
-        probe, _ = enomr.probe_fp64_fma(iters=20000, device=dev)
+        probe, probe_ops = probe_ops_peak(enomr, dev)
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        clocks_t = clk.summary("timed_start", "timed_end")
+        mhz = clocks_t.get("sm_mhz") or clocks_t.get("sm_max_mhz") or 2070.0
         # 2 FP64 lanes per SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
         # peak_sustained = 2 / SM / cycle; DMUL and DADD take the same slots), at the
         # median SM clock of the timed region
@@ -640,101 +924,74 @@ def main_ours(a):
         x_avg = x_ms / max(nx_launch, 1)
         y_avg = y_ms / max(ny_launch, 1)
         if x_avg >= y_avg:
-            dom, avg, (fl, ops) = 0, x_avg, wx
+            dom, avg, (fl, ops), (mfl, mops) = 0, x_avg, wx, mx
         else:
-            dom, avg, (fl, ops) = 1, y_avg, wy
-        kname = f"k_sweep<{R},4,{dom}>"
+            dom, avg, (fl, ops), (mfl, mops) = 1, y_avg, wy, my
+        kname = f"k_sweep_tma<{R},{dom}>"
         achieved = ops / (avg * 1e-3)
         extras["roofline"] = {
             "bound": "alu", "pipe": "fp64", "kernel": kname,
             "achieved": round(achieved / 1e9, 2), "peak": round(peak_ops / 1e9, 2),
             "unit": "GFP64op/s", "frac": round(achieved / peak_ops, 4),
+            "frac_executed": round(achieved / peak_ops, 4),
+            "frac_method": round(mops / (avg * 1e-3) / peak_ops, 4),
+            "frac_definitions": {
+                "frac_executed": "the work the kernel executes (flat interfaces on one state "
+                                 "take the cell's flux, repeated cells copy their "
+                                 "representative's values), over the unit-count peak",
+                "frac_method": "the method's per-interface work with every interface and "
+                               "cell evaluated in full, over the same peak; above 1 where "
+                               "the shortcuts skip most of it"},
             "peak_source": (f"unit counts x clock: 2 FP64 ops/clk/SM x {sms} SMs x "
                             f"{mhz:.0f} MHz (median SM clock of the timed region)"),
             "op_definition": "fma, mul, add, div, rsqrt = 1 FP64 operation each",
+            "fp64_fma_probe_tflops": round(probe / 1e12, 4),
+            "frac_of_probe": round(achieved / probe_ops, 4),
             "traffic": recorded_traffic(kname, n, R),
             "avg_launch_ms": round(avg, 4), "algorithmic_ops_per_launch": ops,
+            "method_ops_per_launch": mops,
             "algorithmic_flops_per_launch": fl,
             "achieved_tflops": round(fl / (avg * 1e-3) / 1e12, 4),
-            "frac_of_fma_flop_peak": round(fl / (avg * 1e-3) / (2.0 * peak_ops), 4),
-            "fp64_fma_probe_tflops": round(probe / 1e12, 4),
             "x_sweep_ms": round(x_avg, 4), "y_sweep_ms": round(y_avg, 4),
             "x_sweep_frac": round(wx[1] / (x_avg * 1e-3) / peak_ops, 4),
             "y_sweep_frac": round(wy[1] / (y_avg * 1e-3) / peak_ops, 4),
+            "x_sweep_frac_method": round(mx[1] / (x_avg * 1e-3) / peak_ops, 4),
+            "y_sweep_frac_method": round(my[1] / (y_avg * 1e-3) / peak_ops, 4),
             "alpha_ms": round(a_ms / max(na_launch, 1), 4),
             "hbm": hbm_side(n, dom, avg)}
         extras["selection_histogram_x"] = [round(float(v)) for v in hx]
         extras["work_samples"] = ns
-        # every order on the same workload, a smooth workload, and the scalar
-        # advection throughput case (each: 1 warm-up step, 2 timed steps)
-        def rate(solver, Ustate, steps=2, dt=0.0):
-            solver.step(Ustate, dt, a.cfl)
-            torch.cuda.synchronize()
-            f0 = torch.cuda.Event(enable_timing=True)
-            f1 = torch.cuda.Event(enable_timing=True)
-            f0.record()
-            for _ in range(steps):
-                solver.step(Ustate, dt, a.cfl)
-            f1.record()
-            torch.cuda.synchronize()
-            cells = Ustate[0].numel() if Ustate.dim() > 1 else Ustate.numel()
-            return cells * 3 * steps / (f0.elapsed_time(f1) * 1e-3)
+        extras["staging_ab"] = staging_ab(enomr, s, U0, dev, min(a.steps, 10), a.cfl)
         per_order, per_order_frac = {}, {}
         for Rk in enomr.ORDERS:
             sk = enomr.Solver(enomr.EULER, (n, n), order=Rk, dx=dx, dy=dy,
                               bc=enomr.TRANSMISSIVE, device=dev)
             Uk = torch.from_numpy(U0).to(dev)
-            per_order[str(Rk)] = rate(sk, Uk)
-            per_order_frac[str(Rk)] = sweep_fracs(enomr, sk, Uk, Rk, n, a.cfl, peak_ops)
+            per_order[str(Rk)] = rate_of(sk, Uk, cfl=a.cfl)
+            per_order_frac[str(Rk)] = sweep_fracs(enomr, sk, Uk, Rk, n, a.cfl, peak_ops,
+                                                  probe_ops=probe_ops)
             sk.close()
+            del Uk
         extras["per_order_riemann"] = {"unit": UNIT, "values": per_order,
                                        "fp64_op_frac": per_order_frac,
                                        "run": "1 warm-up + 2 timed steps from t = 0; "
                                               "fractions over the next 2 steps"}
-        Uv, hv, _ = workloads.isentropic_vortex(n)
-        sv = enomr.Solver(enomr.EULER, (n, n), order=R, dx=hv, dy=hv, bc=enomr.PERIODIC,
-                          device=dev)
-        Uvd = torch.from_numpy(Uv).to(dev)
-        extras["smooth_vortex"] = {"workload": f"isentropic vortex {n}^2 periodic, order {R}",
-                                   "value": rate(sv, Uvd), "unit": UNIT,
-                                   "fp64_op_frac": sweep_fracs(enomr, sv, Uvd, R, n, a.cfl,
-                                                               peak_ops)}
-        sv.close()
+        extras["per_order_vortex"] = per_order_vortex(enomr, workloads, dev, n, a.cfl, peak_ops,
+                                                      probe_ops)
+        extras["riemann_sizes"] = riemann_sizes(enomr, workloads, dev, a.cfl)
     if rank == 0 and not a.no_extras and a.paper_runs:
         extras.update(paper_runs(enomr, workloads, dev, R))
     if rank == 0 and not a.no_extras:
-        adv = {}
-        for Rk in (5, 9, 17):
-            ua, ha = workloads.advection_sine(1 << 24)
-            sa = enomr.Solver(enomr.ADVECTION, 1 << 24, order=Rk, dx=ha, bc=enomr.PERIODIC,
-                              device=dev)
-            ud = torch.from_numpy(ua).to(dev).view(1, -1).squeeze(0)
-            sa.step(ud, 0.5 * ha)
-            torch.cuda.synchronize()
-            f0 = torch.cuda.Event(enable_timing=True)
-            f1 = torch.cuda.Event(enable_timing=True)
-            f0.record()
-            for _ in range(4):
-                sa.step(ud, 0.5 * ha)
-            f1.record()
-            torch.cuda.synchronize()
-            adv[str(Rk)] = ua.size * 3 * 4 / (f0.elapsed_time(f1) * 1e-3)
-            sa.close()
-        extras["advection_2p24"] = {"workload": "advection sin(pi x), N=2^24, periodic",
-                                    "unit": UNIT, "values": adv}
-        burg = {}
-        for Rk in (5, 9, 17):
-            ub, hb = workloads.burgers_sine3(1 << 24)
-            sb = enomr.Solver(enomr.BURGERS, 1 << 24, order=Rk, dx=hb, bc=enomr.PERIODIC,
-                              device=dev)
-            burg[str(Rk)] = rate(sb, torch.from_numpy(ub).to(dev), steps=4)
-            sb.close()
-        extras["burgers_2p24"] = {"workload": "Burgers 1 + 0.5 sin^3(pi x) on [0,2], N=2^24, "
-                                              "periodic, CFL 0.5 steps",
-                                  "unit": UNIT, "values": burg}
+        hbm_peak = hbm_side(n, 0, 1.0)["peak_gbs"]
+        extras.update(scalar_fracs(enomr, workloads, dev, peak_ops, hbm_peak))
+        extras["small_configs"] = small_configs(enomr, workloads, dev)
         extras["batched"] = batched_gain(enomr, workloads, dev, a)
-        extras["adjoint"] = adjoint_ratio(enomr, workloads, dev)
+        extras["adjoint"] = {"n512": adjoint_ratio(enomr, workloads, dev, n=512),
+                             "n1024": adjoint_ratio(enomr, workloads, dev, n=1024)}
         extras["e2e"] = end_to_end(s, U0, U, cells, a)
+    clocks_all = clk.stop()
+    clocks = clk.summary("timed_start", "timed_end")
+    clocks["whole_run"] = clocks_all
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -746,7 +1003,9 @@ def main_ours(a):
         out.update(extras)
         if not a.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(a)
+            out["parity"] = parity_check(a, enomr, s, U_final, dx, dy)
         print(json.dumps(out), flush=True)
+    s.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -801,6 +1060,36 @@ def cpu_baseline(a, budget_s=20.0):
                       f"{m}x{m} grid ({el:.1f} s wall)",
             "single_thread": {"value": m1 * m1 * 3 / el1, "unit": UNIT, "cores": 1,
                               "sample": f"one step on a {m1}x{m1} grid ({el1:.1f} s wall)"}}
+
+
+def parity_check(a, enomr, s, U, dx, dy):
+    """The CUDA path against the oracle on the final state of the timed run
+    (seed 0, the full grid; part of the CPU leg): selection flips of one
+    right-hand side (every interface, field and side of both sweeps) and the
+    largest difference of the right-hand side against the oracle re-run
+    with the CUDA path's selections, relative to max(||L||, ||F||/h)."""
+    import oracle
+    t0 = time.perf_counter()
+    sel = s.selection(U).cpu().numpy()
+    rhs = s.rhs(U).cpu().numpy()
+    Uh = U.cpu().numpy()
+    ref = oracle.rhs_euler2d(Uh, dx, dy, a.order, bc=oracle.BC_TRANSMISSIVE, want_sel=True)
+    flips = int((ref["sel"] != sel).sum())
+    forced = oracle.rhs_euler2d(Uh, dx, dy, a.order, bc=oracle.BC_TRANSMISSIVE, forced=sel)["rhs"]
+    rho, mx, my, E = Uh
+    u, v = mx / rho, my / rho
+    p = 0.4 * (E - 0.5 * rho * (u * u + v * v))
+    fscale = max(float(np.abs(mx).max()), float(np.abs(my).max()),
+                 float(np.abs(mx * u + p).max()), float(np.abs(my * v + p).max()),
+                 float(np.abs((E + p) * u).max()), float(np.abs((E + p) * v).max()))
+    lnorm = float(np.abs(forced).max())
+    err = float(np.abs(rhs - forced).max())
+    return {"state": f"final state of the timed run ({a.steps} steps, seed 0, {a.n}^2)",
+            "selection_flips": flips, "selections": int(sel.size),
+            "rhs_max_abs_diff": err,
+            "rhs_rel_diff": err / max(lnorm, fscale / min(dx, dy)),
+            "rhs_rel_diff_vs_L": err / lnorm if lnorm > 0 else 0.0,
+            "wall_s": round(time.perf_counter() - t0, 1)}
 
 
 def main_reference(a):

@@ -235,6 +235,22 @@ enum { ENOMR_STAGING_AUTO = 0, ENOMR_STAGING_LOADS = 1, ENOMR_STAGING_TMA = 2 };
 ENOMR_API enomr_status enomr_set_staging(enomr_ctx *ctx, int mode);
 
 /*
+ * enomr_set_occupancy -- which instance of the 2D Euler sweeps runs:
+ *   ENOMR_OCCUPANCY_HIGH  many warps per SM (40 with plain loads, 32 with
+ *                         TMA), few registers per thread: hides latency on
+ *                         large grids dominated by flat interfaces;
+ *   ENOMR_OCCUPANCY_LOW   16 warps per SM, 128 registers per thread (the
+ *                         long path's windows stay in registers): for grids
+ *                         of few tiles, whose launches last as long as a
+ *                         few tiles in sequence;
+ *   ENOMR_OCCUPANCY_AUTO  (default) LOW when the x sweep has fewer tiles
+ *                         than two waves of the HIGH instance, else HIGH.
+ * Same results bit for bit.  Host-only setting, no synchronisation.
+ */
+enum { ENOMR_OCCUPANCY_AUTO = 0, ENOMR_OCCUPANCY_HIGH = 1, ENOMR_OCCUPANCY_LOW = 2 };
+ENOMR_API enomr_status enomr_set_occupancy(enomr_ctx *ctx, int mode);
+
+/*
  * Adjoint.  With the discrete choices of the forward pass frozen -- the
  * stencil (or minmod branch) chosen at every interface, field and side, and
  * the cell attaining each per-line alpha -- L is a smooth function of U.
@@ -270,6 +286,16 @@ ENOMR_API enomr_status enomr_debug_alpha(enomr_ctx *ctx, double *alpha_x, double
  */
 ENOMR_API enomr_status enomr_step_vjp(enomr_ctx *ctx, const double *U_n, double dt,
                                       const double *U_np1_bar, double *U_n_bar);
+
+/*
+ * enomr_step_vjp_cfl -- as enomr_step_vjp for a step that enomr_step took
+ *   with its CFL dt (dt <= 0, cfl > 0): the dt is recomputed on the device
+ *   from U_n by the same kernels (so it is the forward step's dt bit for
+ *   bit) and held fixed.  No host synchronisation, so a long adjoint sweep
+ *   runs without a round trip per step.
+ */
+ENOMR_API enomr_status enomr_step_vjp_cfl(enomr_ctx *ctx, const double *U_n, double cfl,
+                                          const double *U_np1_bar, double *U_n_bar);
 
 /*
  * Batched problems: many independent 1D Euler problems of uneven size

@@ -47,6 +47,9 @@ struct enomr_ctx {
     double *t_dev;
     // staging of the 2D sweeps: ENOMR_STAGING_AUTO / _LOADS / _TMA
     int staging;
+    // occupancy of the 2D sweeps: ENOMR_OCCUPANCY_AUTO / _HIGH / _LOW
+    int occupancy;
+    int sms;  // SMs of the device the context was created on
 };
 
 static void prof_start(enomr_ctx *c, int k)
@@ -363,27 +366,39 @@ template <int R> struct E1F {
     static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler1d<R>(a, s); }
 };
 template <int R> struct E2XF {
-    static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler2d_x<R>(a, s); }
+    static cudaError_t run(const SweepArgs &a, bool low, cudaStream_t s)
+    {
+        return launch_euler2d_x<R>(a, low, s);
+    }
 };
 template <int R> struct E2XEF {
-    static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler2d_x_ext<R>(a, s); }
+    static cudaError_t run(const SweepArgs &a, bool low, cudaStream_t s)
+    {
+        return launch_euler2d_x_ext<R>(a, low, s);
+    }
 };
 template <int R> struct E2YEF {
-    static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler2d_y_ext<R>(a, s); }
+    static cudaError_t run(const SweepArgs &a, bool low, cudaStream_t s)
+    {
+        return launch_euler2d_y_ext<R>(a, low, s);
+    }
 };
 template <int R> struct E2YF {
-    static cudaError_t run(const SweepArgs &a, cudaStream_t s) { return launch_euler2d_y<R>(a, s); }
+    static cudaError_t run(const SweepArgs &a, bool low, cudaStream_t s)
+    {
+        return launch_euler2d_y<R>(a, low, s);
+    }
 };
 template <int R> struct E2XTF {
-    static cudaError_t run(const CUtensorMap &m, const SweepArgs &a, cudaStream_t s)
+    static cudaError_t run(const CUtensorMap &m, const SweepArgs &a, bool low, cudaStream_t s)
     {
-        return launch_euler2d_x_tma<R>(m, a, s);
+        return launch_euler2d_x_tma<R>(m, a, low, s);
     }
 };
 template <int R> struct E2YTF {
-    static cudaError_t run(const CUtensorMap &m, const SweepArgs &a, cudaStream_t s)
+    static cudaError_t run(const CUtensorMap &m, const SweepArgs &a, bool low, cudaStream_t s)
     {
-        return launch_euler2d_y_tma<R>(m, a, s);
+        return launch_euler2d_y_tma<R>(m, a, low, s);
     }
 };
 
@@ -434,9 +449,10 @@ template <int R> struct VjpF {
     }
 };
 template <int R> struct AdvVjpF {
-    static cudaError_t run(const AdvArgs &a, const double *Lb, double *Ub, double sc, cudaStream_t s)
+    static cudaError_t run(const AdvArgs &a, const double *Lb, double *Ub, double sc,
+                           const double *sc_dev, cudaStream_t s)
     {
-        return launch_advection_vjp<R>(a, Lb, Ub, sc, s);
+        return launch_advection_vjp<R>(a, Lb, Ub, sc, sc_dev, s);
     }
 };
 
@@ -521,6 +537,17 @@ static bool extended(const enomr_ctx *c)
     return c->custom_sides || c->gx != 0.0 || c->gy != 0.0;
 }
 
+// The 2D sweeps' low-occupancy instances: forced, or (automatic) for grids
+// whose x sweep has fewer tiles than two waves of the high-occupancy
+// instance, where a launch's time is that of a few tiles in sequence.
+static bool low_occupancy(const enomr_ctx *c)
+{
+    if (c->occupancy == ENOMR_OCCUPANCY_LOW) return true;
+    if (c->occupancy == ENOMR_OCCUPANCY_HIGH) return false;
+    const long long tiles = ((c->nx + X_TP - 2) / (X_TP - 1)) * ((c->ny + X_NL - 1) / X_NL);
+    return tiles < 2LL * c->sms * (SWEEP_HIGH_THREADS_PER_SM / (X_TP * X_NL));
+}
+
 // Evaluate L(U) into the epilogue.  The alpha of U must be current.
 static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilogue &epi,
                                       uint8_t *sel, double *ft = nullptr, double t_coef = 0.0)
@@ -559,6 +586,7 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     const bool tma = !ext && c->staging != ENOMR_STAGING_LOADS && state_map(c, U, 0, &mx) &&
                      state_map(c, U, 1, &my);
     if (c->staging == ENOMR_STAGING_TMA && !tma) return ENOMR_EINVAL;
+    const bool low = low_occupancy(c);
     SweepArgs ax = sweep_args(c, U, false);
     ax.sel = sel;
     ax.ft_out = ft;
@@ -566,9 +594,9 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     ax.epi.out = c->D;
     ax.t_coef = t_coef;
     prof_start(c, 1);
-    cudaError_t e = ext   ? by_order<E2XEF>(c->order, ax, c->stream)
-                    : tma ? by_order<E2XTF>(c->order, mx, ax, c->stream)
-                          : by_order<E2XF>(c->order, ax, c->stream);
+    cudaError_t e = ext   ? by_order<E2XEF>(c->order, ax, low, c->stream)
+                    : tma ? by_order<E2XTF>(c->order, mx, ax, low, c->stream)
+                          : by_order<E2XF>(c->order, ax, low, c->stream);
     prof_stop(c, 1);
     CU_TRY(e);
     SweepArgs ay = sweep_args(c, U, true);
@@ -578,9 +606,9 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     ay.epi.Dprev = c->D;
     ay.t_coef = t_coef;
     prof_start(c, 2);
-    e = ext   ? by_order<E2YEF>(c->order, ay, c->stream)
-        : tma ? by_order<E2YTF>(c->order, my, ay, c->stream)
-              : by_order<E2YF>(c->order, ay, c->stream);
+    e = ext   ? by_order<E2YEF>(c->order, ay, low, c->stream)
+        : tma ? by_order<E2YTF>(c->order, my, ay, low, c->stream)
+              : by_order<E2YF>(c->order, ay, low, c->stream);
     prof_stop(c, 2);
     return cu(e);
 }
@@ -703,6 +731,15 @@ ENOMR_API enomr_status enomr_init(enomr_ctx **out, int eq, int ndim, int64_t nx,
         cudaGetLastError();
         enomr_free(c);
         return ENOMR_ENOMEM;
+    }
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            enomr_free(c);
+            return ENOMR_ECUDA;
+        }
+        c->sms = sms;
     }
     if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->t_dev, 0, sizeof(double)) != cudaSuccess ||
@@ -910,9 +947,18 @@ ENOMR_API enomr_status enomr_set_staging(enomr_ctx *c, int mode)
     return ENOMR_OK;
 }
 
+ENOMR_API enomr_status enomr_set_occupancy(enomr_ctx *c, int mode)
+{
+    if (!c || mode < ENOMR_OCCUPANCY_AUTO || mode > ENOMR_OCCUPANCY_LOW) return ENOMR_EINVAL;
+    c->occupancy = mode;
+    return ENOMR_OK;
+}
+
+// Ubar += scale * J(U)^T Lbar, scale = factor * (*factor_dev if given).
 static enomr_status rhs_vjp_impl(enomr_ctx *c, const double *U, const double *Lbar, double *Ubar,
                                  double scale, const uint8_t *sel_in = nullptr,
-                                 const double *ft_in = nullptr)
+                                 const double *ft_in = nullptr,
+                                 const double *scale_dev = nullptr)
 {
     if (c->eq == ENOMR_ADVECTION) {
         AdvArgs a;
@@ -922,7 +968,7 @@ static enomr_status rhs_vjp_impl(enomr_ctx *c, const double *U, const double *Lb
         a.bc = c->bc;
         a.a = c->adv;
         a.inv_h = 1.0 / c->dx;
-        return cu(by_order<AdvVjpF>(c->order, a, Lbar, Ubar, scale, c->stream));
+        return cu(by_order<AdvVjpF>(c->order, a, Lbar, Ubar, scale, scale_dev, c->stream));
     }
     const int C = c->ndim == 2 ? 4 : 3;
     enomr_status st = compute_alpha(c, U, false);
@@ -958,6 +1004,7 @@ static enomr_status rhs_vjp_impl(enomr_ctx *c, const double *U, const double *Lb
     v.inv_gm1 = 1.0 / (c->gamma - 1.0);
     v.gamma = c->gamma;
     v.scale = scale;
+    v.scale_dev = scale_dev;
     v.status = c->status;
     v.inv_h = 1.0 / c->dx;
     v.alpha = c->ax;
@@ -1000,15 +1047,38 @@ ENOMR_API enomr_status enomr_rhs_vjp(enomr_ctx *c, const double *U, const double
     return rhs_vjp_impl(c, U, Lbar, Ubar, scale);
 }
 
+// Transpose of one SSP-RK3 step from U^n whose dt is already in c->dt.
+static enomr_status step_vjp_impl(enomr_ctx *c, const double *Un, const double *Ubar_np1,
+                                  double *Ubar_n);
+
 ENOMR_API enomr_status enomr_step_vjp(enomr_ctx *c, const double *Un, double dt,
                                       const double *Ubar_np1, double *Ubar_n)
 {
     if (!c || !Un || !Ubar_np1 || !Ubar_n || !(dt > 0.0)) return ENOMR_EINVAL;
     if (c->eq == ENOMR_BURGERS || extended(c)) return ENOMR_EINVAL;
     if ((const double *)Ubar_n == Ubar_np1 || (const double *)Ubar_n == Un) return ENOMR_EINVAL;
+    CU_TRY(launch_set_dt(c->smax, 0.0, dt, c->dt, c->stream));
+    return step_vjp_impl(c, Un, Ubar_np1, Ubar_n);
+}
+
+ENOMR_API enomr_status enomr_step_vjp_cfl(enomr_ctx *c, const double *Un, double cfl,
+                                          const double *Ubar_np1, double *Ubar_n)
+{
+    if (!c || !Un || !Ubar_np1 || !Ubar_n || !(cfl > 0.0)) return ENOMR_EINVAL;
+    if (c->eq == ENOMR_BURGERS || extended(c)) return ENOMR_EINVAL;
+    if ((const double *)Ubar_n == Ubar_np1 || (const double *)Ubar_n == Un) return ENOMR_EINVAL;
+    // the forward step's dt, recomputed from U^n by the same kernels: the
+    // same bits, without a host round trip
+    enomr_status st = set_step_dt(c, Un, 0.0, cfl);
+    if (st) return st;
+    return step_vjp_impl(c, Un, Ubar_np1, Ubar_n);
+}
+
+static enomr_status step_vjp_impl(enomr_ctx *c, const double *Un, const double *Ubar_np1,
+                                  double *Ubar_n)
+{
     enomr_status st;
     // recompute the stages from the step's checkpoint U^n
-    CU_TRY(launch_set_dt(c->smax, 0.0, dt, c->dt, c->stream));
     // the recomputed stages also keep their selections and per-field values,
     // which the transposes at U^n and U^(1) then reuse
     const bool keep = c->eq == ENOMR_EULER;
@@ -1021,17 +1091,20 @@ ENOMR_API enomr_status enomr_step_vjp(enomr_ctx *c, const double *Un, double dt,
     // U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2))
     if ((st = axpy(c, 1.0 / 3.0, Ubar_np1, Ubar_n, 0))) return st;
     if ((st = axpy(c, 2.0 / 3.0, Ubar_np1, c->Ub2, 0))) return st;
-    if ((st = rhs_vjp_impl(c, c->U2, Ubar_np1, c->Ub2, 2.0 / 3.0 * dt))) return st;
+    // the step's dt is on the device (c->dt): the cotangent scales are
+    // formed there, (2/3) dt, (1/4) dt and dt
+    if ((st = rhs_vjp_impl(c, c->U2, Ubar_np1, c->Ub2, 2.0 / 3.0, nullptr, nullptr, c->dt)))
+        return st;
     // U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
     if ((st = axpy(c, 0.75, c->Ub2, Ubar_n, 1))) return st;
     if ((st = axpy(c, 0.25, c->Ub2, c->Ub1, 0))) return st;
-    if ((st = rhs_vjp_impl(c, c->U1, c->Ub2, c->Ub1, 0.25 * dt, keep ? c->fsel[1] : nullptr,
-                           keep ? c->fft[1] : nullptr)))
+    if ((st = rhs_vjp_impl(c, c->U1, c->Ub2, c->Ub1, 0.25, keep ? c->fsel[1] : nullptr,
+                           keep ? c->fft[1] : nullptr, c->dt)))
         return st;
     // U1 = U^n + dt L(U^n)
     if ((st = axpy(c, 1.0, c->Ub1, Ubar_n, 1))) return st;
-    return rhs_vjp_impl(c, Un, c->Ub1, Ubar_n, dt, keep ? c->fsel[0] : nullptr,
-                        keep ? c->fft[0] : nullptr);
+    return rhs_vjp_impl(c, Un, c->Ub1, Ubar_n, 1.0, keep ? c->fsel[0] : nullptr,
+                        keep ? c->fft[0] : nullptr, c->dt);
 }
 
 ENOMR_API enomr_status enomr_debug_alpha(enomr_ctx *c, double *alpha_x, double *alpha_y,

@@ -11,6 +11,9 @@ namespace enomr {
 // a tile copy of the TMA sweeps ran out and the launch stopped early).
 enum : int { ST_NONPHYS_CELL = 1, ST_NONPHYS_ROE = 2, ST_TMA_TIMEOUT = 8 };
 
+// Resident threads per SM of the high-occupancy sweep instances.
+constexpr int SWEEP_HIGH_THREADS_PER_SM = 1280;
+
 // Tile shapes of the sweeps (interfaces per line x lines per CTA).
 constexpr int E1_TP = 64;
 constexpr int X_TP = 128, X_NL = 2;
@@ -132,19 +135,20 @@ cudaError_t launch_batch_dt(const double *alpha, const double *inv_dx, double cf
 template <int R> cudaError_t launch_advection(const AdvArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_burgers(const AdvArgs &a, cudaStream_t s);
 template <int R> cudaError_t launch_euler1d(const SweepArgs &a, cudaStream_t s);
-template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, cudaStream_t s);
-template <int R> cudaError_t launch_euler2d_x_ext(const SweepArgs &a, cudaStream_t s);
-template <int R> cudaError_t launch_euler2d_y_ext(const SweepArgs &a, cudaStream_t s);
-template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, cudaStream_t s);
+// the 2D sweeps; low: the low-occupancy instance (more registers per thread)
+template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, bool low, cudaStream_t s);
+template <int R> cudaError_t launch_euler2d_x_ext(const SweepArgs &a, bool low, cudaStream_t s);
+template <int R> cudaError_t launch_euler2d_y_ext(const SweepArgs &a, bool low, cudaStream_t s);
+template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, bool low, cudaStream_t s);
 }  // namespace enomr
 
 // the sweeps staged by the Tensor Memory Accelerator (enomr_tma.cuh)
 struct CUtensorMap_st;
 namespace enomr {
 template <int R> cudaError_t launch_euler2d_x_tma(const CUtensorMap_st &map, const SweepArgs &a,
-                                                  cudaStream_t s);
+                                                  bool low, cudaStream_t s);
 template <int R> cudaError_t launch_euler2d_y_tma(const CUtensorMap_st &map, const SweepArgs &a,
-                                                  cudaStream_t s);
+                                                  bool low, cudaStream_t s);
 // Box extents {x, y, components} of the tile copies of the TMA sweeps: the
 // x sweep copies TP + 2g cells (an even count) of X_NL rows, the y sweep
 // Y_NL columns of TP + 2g - 1 cells; g = (order + 1) / 2.
@@ -163,6 +167,7 @@ struct VjpArgs {
     long long nx, ny;
     int bc;
     double gm1, inv_gm1, gamma, inv_h, scale;
+    const double *scale_dev;  // if set, the cotangent scale is scale * *scale_dev
     const double *alpha;  // [lines][3]
     double *alpha_bar;    // [lines][3], accumulated
     int *status;
@@ -175,7 +180,8 @@ struct VjpArgs {
 
 template <int R> cudaError_t launch_sweep_vjp(const VjpArgs &a, int C, int dir, cudaStream_t s);
 template <int R> cudaError_t launch_advection_vjp(const AdvArgs &a, const double *Lbar,
-                                                  double *Ubar, double scale, cudaStream_t s);
+                                                  double *Ubar, double scale,
+                                                  const double *scale_dev, cudaStream_t s);
 
 cudaError_t launch_alpha(int C, const AlphaArgs &a, cudaStream_t s);
 cudaError_t launch_scalar_speed(const double *U, long long n, double inv_dx, double *speed,

@@ -39,9 +39,16 @@ __device__ __forceinline__ long long abits(double x)
 __device__ __forceinline__ long long imax64(long long a, long long b) { return a > b ? a : b; }
 __device__ __forceinline__ long long imin64(long long a, long long b) { return a < b ? a : b; }
 
+// Cell of (possibly ghost) index i on a line of n cells: periodic wrap
+// (bc 0) or clamp (bc 1).  A tile's cells lie within one line length of the
+// line in all but the shortest lines, so the wrap is one add or subtract
+// there; the 64-bit remainder (a long software sequence) only beyond.
 __device__ __forceinline__ long long ghost(long long i, long long n, int bc)
 {
     if (bc == 0) {
+        if (i >= 0 && i < n) return i;
+        if (i < 0 && i >= -n) return i + n;
+        if (i >= n && i < 2 * n) return i - n;
         long long r = i % n;
         return r < 0 ? r + n : r;
     }

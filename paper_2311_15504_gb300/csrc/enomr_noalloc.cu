@@ -61,11 +61,11 @@ cudaError_t scratch_address(cudaStream_t s, double **out)
 
 template <int R> cudaError_t run_x(const enomr::SweepArgs &a, cudaStream_t s)
 {
-    return enomr::launch_euler2d_x<R>(a, s);
+    return enomr::launch_euler2d_x<R>(a, false, s);
 }
 template <int R> cudaError_t run_y(const enomr::SweepArgs &a, cudaStream_t s)
 {
-    return enomr::launch_euler2d_y<R>(a, s);
+    return enomr::launch_euler2d_y<R>(a, false, s);
 }
 
 cudaError_t sweep(bool ysweep, int R, const enomr::SweepArgs &a, cudaStream_t s)

@@ -34,19 +34,31 @@ template <int R> cudaError_t launch_euler1d(const SweepArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, cudaStream_t s)
+// Tiles of the 2D sweeps (the grid of one launch of the loading instances).
+inline dim3 grid_x(const SweepArgs &a)
 {
-    const long long tx = (a.nx + X_TP - 2) / (X_TP - 1);
-    const long long ty = (a.ny + X_NL - 1) / X_NL;
-    k_sweep<R, 4, 0, X_TP, X_NL><<<dim3((unsigned)tx, (unsigned)ty), X_TP * X_NL, 0, s>>>(a);
+    return dim3((unsigned)((a.nx + X_TP - 2) / (X_TP - 1)), (unsigned)((a.ny + X_NL - 1) / X_NL));
+}
+inline dim3 grid_y(const SweepArgs &a)
+{
+    return dim3((unsigned)((a.nx + Y_NL - 1) / Y_NL), (unsigned)((a.ny + Y_TP - 2) / (Y_TP - 1)));
+}
+
+template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, bool low, cudaStream_t s)
+{
+    if (low)
+        k_sweep<R, 4, 0, X_TP, X_NL, false, SWEEP_LOW_CTAS><<<grid_x(a), X_TP * X_NL, 0, s>>>(a);
+    else
+        k_sweep<R, 4, 0, X_TP, X_NL><<<grid_x(a), X_TP * X_NL, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, cudaStream_t s)
+template <int R> cudaError_t launch_euler2d_y(const SweepArgs &a, bool low, cudaStream_t s)
 {
-    const long long tx = (a.nx + Y_NL - 1) / Y_NL;
-    const long long ty = (a.ny + Y_TP - 2) / (Y_TP - 1);
-    k_sweep<R, 4, 1, Y_TP, Y_NL><<<dim3((unsigned)tx, (unsigned)ty), Y_TP * Y_NL, 0, s>>>(a);
+    if (low)
+        k_sweep<R, 4, 1, Y_TP, Y_NL, false, SWEEP_LOW_CTAS><<<grid_y(a), Y_TP * Y_NL, 0, s>>>(a);
+    else
+        k_sweep<R, 4, 1, Y_TP, Y_NL><<<grid_y(a), Y_TP * Y_NL, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -54,26 +66,28 @@ template cudaError_t launch_advection<ENOMR_R>(const AdvArgs &, cudaStream_t);
 template cudaError_t launch_burgers<ENOMR_R>(const AdvArgs &, cudaStream_t);
 template cudaError_t launch_euler1d<ENOMR_R>(const SweepArgs &, cudaStream_t);
 // with boundary sides / body force (the 2D problems of Sec. 4.4)
-template <int R> cudaError_t launch_euler2d_x_ext(const SweepArgs &a, cudaStream_t s)
+template <int R> cudaError_t launch_euler2d_x_ext(const SweepArgs &a, bool low, cudaStream_t s)
 {
-    const long long tx = (a.nx + X_TP - 2) / (X_TP - 1);
-    const long long ty = (a.ny + X_NL - 1) / X_NL;
-    k_sweep<R, 4, 0, X_TP, X_NL, true><<<dim3((unsigned)tx, (unsigned)ty), X_TP * X_NL, 0, s>>>(a);
+    if (low)
+        k_sweep<R, 4, 0, X_TP, X_NL, true, SWEEP_LOW_CTAS><<<grid_x(a), X_TP * X_NL, 0, s>>>(a);
+    else
+        k_sweep<R, 4, 0, X_TP, X_NL, true><<<grid_x(a), X_TP * X_NL, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int R> cudaError_t launch_euler2d_y_ext(const SweepArgs &a, cudaStream_t s)
+template <int R> cudaError_t launch_euler2d_y_ext(const SweepArgs &a, bool low, cudaStream_t s)
 {
-    const long long tx = (a.nx + Y_NL - 1) / Y_NL;
-    const long long ty = (a.ny + Y_TP - 2) / (Y_TP - 1);
-    k_sweep<R, 4, 1, Y_TP, Y_NL, true><<<dim3((unsigned)tx, (unsigned)ty), Y_TP * Y_NL, 0, s>>>(a);
+    if (low)
+        k_sweep<R, 4, 1, Y_TP, Y_NL, true, SWEEP_LOW_CTAS><<<grid_y(a), Y_TP * Y_NL, 0, s>>>(a);
+    else
+        k_sweep<R, 4, 1, Y_TP, Y_NL, true><<<grid_y(a), Y_TP * Y_NL, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_euler2d_x<ENOMR_R>(const SweepArgs &, cudaStream_t);
-template cudaError_t launch_euler2d_y<ENOMR_R>(const SweepArgs &, cudaStream_t);
-template cudaError_t launch_euler2d_x_ext<ENOMR_R>(const SweepArgs &, cudaStream_t);
-template cudaError_t launch_euler2d_y_ext<ENOMR_R>(const SweepArgs &, cudaStream_t);
+template cudaError_t launch_euler2d_x<ENOMR_R>(const SweepArgs &, bool, cudaStream_t);
+template cudaError_t launch_euler2d_y<ENOMR_R>(const SweepArgs &, bool, cudaStream_t);
+template cudaError_t launch_euler2d_x_ext<ENOMR_R>(const SweepArgs &, bool, cudaStream_t);
+template cudaError_t launch_euler2d_y_ext<ENOMR_R>(const SweepArgs &, bool, cudaStream_t);
 
 }  // namespace enomr
 
@@ -114,36 +128,39 @@ template <int R> cudaError_t launch_sweep_vjp(const VjpArgs &a, int C, int dir, 
 }
 
 template <int R> cudaError_t launch_advection_vjp(const AdvArgs &a, const double *Lbar, double *Ubar,
-                                                  double scale, cudaStream_t s)
+                                                  double scale, const double *scale_dev,
+                                                  cudaStream_t s)
 {
     const long long tiles = (a.n + ADV_TP - 2) / (ADV_TP - 1);
-    k_advection_vjp<R, ADV_TP><<<(unsigned)tiles, ADV_TP, 0, s>>>(a, Lbar, Ubar, scale);
+    k_advection_vjp<R, ADV_TP><<<(unsigned)tiles, ADV_TP, 0, s>>>(a, Lbar, Ubar, scale, scale_dev);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_sweep_vjp<ENOMR_R>(const VjpArgs &, int, int, cudaStream_t);
 template cudaError_t launch_advection_vjp<ENOMR_R>(const AdvArgs &, const double *, double *, double,
-                                                   cudaStream_t);
+                                                   const double *, cudaStream_t);
 
 }  // namespace enomr
 
 namespace enomr {
 
 template <int R> cudaError_t launch_euler2d_x_tma(const CUtensorMap &map, const SweepArgs &a,
-                                                  cudaStream_t s)
+                                                  bool low, cudaStream_t s)
 {
-    return launch_sweep_tma<R, 0, X_TP, X_NL>(map, a, s);
+    return low ? launch_sweep_tma<R, 0, X_TP, X_NL, SWEEP_LOW_CTAS>(map, a, s)
+               : launch_sweep_tma<R, 0, X_TP, X_NL, TmaCtas<R, 0, X_TP, X_NL>::value>(map, a, s);
 }
 
 template <int R> cudaError_t launch_euler2d_y_tma(const CUtensorMap &map, const SweepArgs &a,
-                                                  cudaStream_t s)
+                                                  bool low, cudaStream_t s)
 {
-    return launch_sweep_tma<R, 1, Y_TP, Y_NL>(map, a, s);
+    return low ? launch_sweep_tma<R, 1, Y_TP, Y_NL, SWEEP_LOW_CTAS>(map, a, s)
+               : launch_sweep_tma<R, 1, Y_TP, Y_NL, TmaCtas<R, 1, Y_TP, Y_NL>::value>(map, a, s);
 }
 
-template cudaError_t launch_euler2d_x_tma<ENOMR_R>(const CUtensorMap &, const SweepArgs &,
+template cudaError_t launch_euler2d_x_tma<ENOMR_R>(const CUtensorMap &, const SweepArgs &, bool,
                                                    cudaStream_t);
-template cudaError_t launch_euler2d_y_tma<ENOMR_R>(const CUtensorMap &, const SweepArgs &,
+template cudaError_t launch_euler2d_y_tma<ENOMR_R>(const CUtensorMap &, const SweepArgs &, bool,
                                                    cudaStream_t);
 
 }  // namespace enomr

@@ -563,10 +563,16 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
 // 3.57 -> 3.70 G cell-updates/s at order 9 (orders 5-17 alike).  The long
 // path spills to local memory (L1) and keeps its speed on the smooth vortex
 // (within 0.5 %).
-constexpr int SWEEP_THREADS_PER_SM = 1280;
+constexpr int SWEEP_THREADS_PER_SM = SWEEP_HIGH_THREADS_PER_SM;
+// The low-occupancy instances (MINB = SWEEP_LOW_CTAS CTAs of 256 threads per
+// SM, 128 registers per thread) keep the long path's windows in registers
+// without spilling; they serve launches of few tiles, whose speed is set by
+// the latency of one tile rather than by the number of warps in flight.
+constexpr int SWEEP_LOW_CTAS = 2;
 
-template <int R, int C, int DIR, int TP, int NL, bool EXT = false>
-__global__ void __launch_bounds__(TP *NL, SWEEP_THREADS_PER_SM / (TP * NL)) k_sweep(SweepArgs A)
+template <int R, int C, int DIR, int TP, int NL, bool EXT = false,
+          int MINB = SWEEP_THREADS_PER_SM / (TP * NL)>
+__global__ void __launch_bounds__(TP *NL, MINB) k_sweep(SweepArgs A)
 {
     constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
     __shared__ SweepSmem<R, C, TP, NL> sm;

@@ -162,9 +162,14 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map,
 // Wait limit of a tile copy: 2^31 cycles, about a second at 2 GHz.
 constexpr long long TMA_WAIT_LIMIT = 1LL << 31;
 
-// CTAs per SM of the TMA sweeps (the shared memory of four ring tiles fits
-// in an SM; 64 registers per thread).
-constexpr int TMA_CTAS_PER_SM = 4;
+// CTAs per SM of the high-occupancy TMA sweeps: five (48 registers per
+// thread, as the loading instances) where five tiles' shared memory fits in
+// an SM (228 KB, 1 KB reserved per CTA), else four (64 registers).
+template <int R, int DIR, int TP, int NL>
+struct TmaCtas {
+    static constexpr int value =
+        5 * (sizeof(TmaSmem<R, 4, DIR, TP, NL>) + 1024) <= 228 * 1024 ? 5 : 4;
+};
 
 template <int R, int DIR, int TP, int NL>
 struct TmaGeom {
@@ -177,8 +182,8 @@ struct TmaGeom {
 // Persistent TMA sweep over ntiles tiles (x sweep: segment-fastest order
 // along the rows; y sweep: column-group-fastest, so that the concurrently
 // processed tiles of a wave share DRAM pages).
-template <int R, int DIR, int TP, int NL>
-__global__ void __launch_bounds__(TP *NL, TMA_CTAS_PER_SM)
+template <int R, int DIR, int TP, int NL, int MINB>
+__global__ void __launch_bounds__(TP *NL, MINB)
     k_sweep_tma(const __grid_constant__ CUtensorMap map, SweepArgs A, long long ntiles)
 {
     constexpr int C = 4;
@@ -194,17 +199,15 @@ __global__ void __launch_bounds__(TP *NL, TMA_CTAS_PER_SM)
     const long long nlines = (DIR == 0) ? ny : nx;
     const long long nseg = G::nseg(nlen), ngrp = G::ngrp(nlines);
 
+    // tile index -> (first interface, first line); the launcher keeps the
+    // tile count below 2^31, so 32-bit division suffices (64-bit division is
+    // a long software sequence)
+    const unsigned nfast = (unsigned)((DIR == 0) ? nseg : ngrp);
     auto tile_of = [&](long long t, long long &x0, long long &l0) {
-        long long seg, grp;
-        if (DIR == 0) {
-            seg = t % nseg;
-            grp = t / nseg;
-        } else {
-            grp = t % ngrp;
-            seg = t / ngrp;
-        }
-        x0 = seg * (TP - 1);
-        l0 = grp * NL;
+        const unsigned tt = (unsigned)t, q = tt / nfast, r = tt - q * nfast;
+        const unsigned seg = (DIR == 0) ? r : q, grp = (DIR == 0) ? q : r;
+        x0 = (long long)seg * (TP - 1);
+        l0 = (long long)grp * NL;
     };
     auto issue = [&](long long t, int slot) {
         long long x0, l0;
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(TP *NL, TMA_CTAS_PER_SM)
 // Host launcher: a persistent grid of (SMs x resident CTAs) CTAs, at most
 // one per tile.  map: tensor map of the state U of a (tiled, 3D: {nx, ny, 4})
 // with this sweep's box.
-template <int R, int DIR, int TP, int NL>
+template <int R, int DIR, int TP, int NL, int MINB>
 cudaError_t launch_sweep_tma(const CUtensorMap &map, const SweepArgs &a, cudaStream_t s)
 {
     using SM = TmaSmem<R, 4, DIR, TP, NL>;
@@ -297,7 +300,7 @@ cudaError_t launch_sweep_tma(const CUtensorMap &map, const SweepArgs &a, cudaStr
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
-    auto k = k_sweep_tma<R, DIR, TP, NL>;
+    auto k = k_sweep_tma<R, DIR, TP, NL, MINB>;
     if (ctas[dev] == 0) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM));
         if (e != cudaSuccess) return e;
@@ -308,10 +311,11 @@ cudaError_t launch_sweep_tma(const CUtensorMap &map, const SweepArgs &a, cudaStr
         if (e != cudaSuccess) return e;
         if (n < 1) return cudaErrorInvalidConfiguration;
         sms[dev] = m;
-        ctas[dev] = n;
+        ctas[dev] = n < MINB ? n : MINB;  // the residency the registers were sized for
     }
     const long long nlen = DIR == 0 ? a.nx : a.ny, nlines = DIR == 0 ? a.ny : a.nx;
     const long long ntiles = G::nseg(nlen) * G::ngrp(nlines);
+    if (ntiles >= (1LL << 31)) return cudaErrorInvalidValue;  // 32-bit tile indices
     long long grid = (long long)sms[dev] * ctas[dev];
     if (grid > ntiles) grid = ntiles;
     k<<<(unsigned)grid, TP * NL, sizeof(SM), s>>>(map, a, ntiles);

@@ -125,10 +125,11 @@ __global__ void __launch_bounds__(TP *NL) k_sweep_vjp(VjpArgs A)
     const int sl = p + g - 1, sr = p + g;
 
     // cotangent of the interface flux: F_k enters L_{k-1} (-1/h) and L_k (+1/h)
+    const double scale = A.scale_dev ? A.scale * *A.scale_dev : A.scale;
     double Fb[C];
 #pragma unroll
     for (int q = 0; q < C; ++q)
-        Fb[q] = owned ? A.scale * (sLb[q][line][p + 1] - sLb[q][line][p]) * A.inv_h : 0.0;
+        Fb[q] = owned ? scale * (sLb[q][line][p + 1] - sLb[q][line][p]) * A.inv_h : 0.0;
 
     // ---- forward: Roe average and scaled eigenvectors (as the forward sweep)
     bool eqLR = true;
@@ -463,8 +464,9 @@ __global__ void __launch_bounds__(TP *NL) k_sweep_vjp(VjpArgs A)
 // transpose scatters a * weight * F_bar_k to the window cells.
 template <int R, int TP>
 __global__ void __launch_bounds__(TP) k_advection_vjp(AdvArgs A, const double *Lbar, double *Ubar,
-                                                     double scale)
+                                                     double factor, const double *factor_dev)
 {
+    const double scale = factor_dev ? factor * *factor_dev : factor;
     constexpr int g = (R + 1) / 2, W = 2 * g - 1, S = TP + 2 * g - 1, T = Tab<R>::T;
     __shared__ double sf[S];
     __shared__ double sA[T * W];

@@ -28,6 +28,8 @@ PERIODIC, TRANSMISSIVE = 0, 1
 ORDERS = (5, 7, 9, 11, 13, 15, 17)
 # staging of the 2D sweeps' tiles (enomr_set_staging)
 STAGING_AUTO, STAGING_LOADS, STAGING_TMA = 0, 1, 2
+# instance of the 2D sweeps (enomr_set_occupancy)
+OCCUPANCY_AUTO, OCCUPANCY_HIGH, OCCUPANCY_LOW = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libenomr.so")
@@ -58,6 +60,7 @@ _SIGS = {
     "enomr_rhs_euler2d_noalloc": (_I, [_P, _P, _L, _L, _D, _D, _I, _D, _I, _P]),
     "enomr_rhs_vjp": (_I, [_P, _P, _P, _P, _D, _I]),
     "enomr_step_vjp": (_I, [_P, _P, _D, _P, _P]),
+    "enomr_step_vjp_cfl": (_I, [_P, _P, _D, _P, _P]),
     "enomr_debug_alpha": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "enomr_batch_init": (_I, [ctypes.POINTER(_P), _L, _P, _P, _I, _D, _I, _P]),
     "enomr_batch_free": (None, [_P]),
@@ -71,6 +74,7 @@ _SIGS = {
     "enomr_set_time": (_I, [_P, _D]),
     "enomr_get_time": (_I, [_P, ctypes.POINTER(_D)]),
     "enomr_set_staging": (_I, [_P, _I]),
+    "enomr_set_occupancy": (_I, [_P, _I]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -239,6 +243,17 @@ class Solver:
                "enomr_step_vjp")
         return out
 
+    def step_vjp_cfl(self, Un, cfl, Ubar_np1, out=None):
+        """As step_vjp for a CFL step (enomr_step with dt <= 0): the step's dt
+        is recomputed on the device from Un (no host round trip)."""
+        if out is None:
+            out = torch.empty_like(Un)
+        self._stream()
+        _check(_lib.enomr_step_vjp_cfl(self._ctx, self._state(Un), float(cfl),
+                                       self._state(Ubar_np1, "Ubar_np1"), self._state(out, "out")),
+               "enomr_step_vjp_cfl")
+        return out
+
     def profile_begin(self, kernel: int, max_launches: int):
         """Time the next launches of one kernel (1 x sweep, 2 y sweep, 3 alpha)."""
         _check(_lib.enomr_profile_begin(self._ctx, kernel, max_launches), "enomr_profile_begin")
@@ -271,6 +286,10 @@ class Solver:
         """STAGING_AUTO (TMA where the state allows it), STAGING_LOADS or
         STAGING_TMA (TMA only; other states raise)."""
         _check(_lib.enomr_set_staging(self._ctx, int(mode)), "enomr_set_staging")
+
+    def set_occupancy(self, mode):
+        """OCCUPANCY_AUTO, OCCUPANCY_HIGH or OCCUPANCY_LOW (2D sweeps)."""
+        _check(_lib.enomr_set_occupancy(self._ctx, int(mode)), "enomr_set_occupancy")
 
     def set_body_force(self, gx, gy):
         _check(_lib.enomr_set_body_force(self._ctx, float(gx), float(gy)),
@@ -368,25 +387,32 @@ class Batch:
 
 
 class _Rollout(torch.autograd.Function):
-    """n SSP-RK3 steps with per-step checkpoints; backward runs enomr_step_vjp
-    step by step in reverse, recomputing the stages from each checkpoint."""
+    """n SSP-RK3 steps with per-step checkpoints (one preallocated
+    [n, *state] tensor); backward runs the step transposes in reverse,
+    recomputing the stages from each checkpoint.  With CFL steps (dt <= 0)
+    every step's dt stays on the device: the forward pass does not read it
+    back and the backward pass recomputes it from the checkpoint
+    (enomr_step_vjp_cfl), so neither direction synchronises per step."""
 
     @staticmethod
     def forward(ctx, U0, solver, nsteps, cfl, dt):
         U = U0.detach().clone()
-        ckpt, dts = [], []
-        for _ in range(nsteps):
-            ckpt.append(U.clone())
-            dts.append(solver.step(U, dt, cfl, return_dt=True))
-        ctx.solver, ctx.ckpt, ctx.dts = solver, ckpt, dts
+        ckpt = torch.empty((nsteps,) + tuple(U.shape), dtype=U.dtype, device=U.device)
+        for i in range(nsteps):
+            ckpt[i].copy_(U)
+            solver.step(U, dt, cfl)
+        ctx.solver, ctx.ckpt, ctx.cfl, ctx.dt = solver, ckpt, cfl, dt
         return U
 
     @staticmethod
     def backward(ctx, gout):
         g = gout.contiguous().clone()
         tmp = torch.empty_like(g)
-        for Un, dt in zip(reversed(ctx.ckpt), reversed(ctx.dts)):
-            ctx.solver.step_vjp(Un, dt, g, out=tmp)
+        for i in reversed(range(ctx.ckpt.shape[0])):
+            if ctx.dt > 0.0:
+                ctx.solver.step_vjp(ctx.ckpt[i], ctx.dt, g, out=tmp)
+            else:
+                ctx.solver.step_vjp_cfl(ctx.ckpt[i], ctx.cfl, g, out=tmp)
             g, tmp = tmp, g
         return g, None, None, None, None
 

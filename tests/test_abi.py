@@ -66,6 +66,7 @@ def test_host_side_argument_checks(lib):
     assert L.enomr_step(None, None, 0.0, 0.5, None) == 1
     assert L.enomr_get_status(None) == 1
     assert L.enomr_set_staging(None, 0) == 1
+    assert L.enomr_set_occupancy(None, 0) == 1
     L.enomr_free(None)
 
 

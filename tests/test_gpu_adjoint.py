@@ -240,3 +240,88 @@ def test_rollout_gradient_vortex(E):
     s = E.Solver(E.EULER, (n, n), order=R, dx=h, dy=h, bc=E.PERIODIC)
     _loss_grad_check(E, s, U0, target, 8,
                      [smooth_dir(U0, 30 + k) * bump[None] for k in range(3)])
+
+
+def test_rollout_gradient_vortex_512_200_steps(E):
+    """The adjoint workload at its stated size: isentropic vortex 512^2 on
+    [0,10]^2 (periodic, order 9), 200 CFL steps with per-step checkpoints,
+    loss 1/2 ||rho(t) - rho_target||^2 with the target's initial density
+    perturbed by 1e-3 N(0,1).  Central differences along 8 seeded directions
+    localised to the vortex core.  The frozen-choice gradient is the
+    derivative only where no selection changes between the +eps and -eps
+    trajectories, so each direction's two trajectories are advanced stage by
+    stage side by side with their selections compared; a direction whose
+    runs differ anywhere is reported and left out (at least 6 of 8 must
+    remain), every other must agree to 1e-6 relative."""
+    import torch
+    n, R, steps = 512, 9, 200
+    h = 10.0 / n
+    centre = (5.0 + 0.37 * h, 5.0 - 0.21 * h)
+    U0, h, _ = wl.isentropic_vortex(n, centre=centre)
+    rng = np.random.Generator(np.random.PCG64(2024))
+    Ut0, _, _ = wl.isentropic_vortex(n, centre=centre)
+    Ut0[0] = Ut0[0] + 1e-3 * rng.standard_normal((n, n))
+    s = E.Solver(E.EULER, (n, n), order=R, dx=h, dy=h, bc=E.PERIODIC)
+    # target run from the perturbed initial density, same step count
+    Ut = torch.from_numpy(Ut0).cuda()
+    for _ in range(steps):
+        s.step(Ut, 0.0, 0.5)
+    tgt = Ut[0].clone()
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    x = torch.from_numpy(U0).cuda().requires_grad_(True)
+    out = E.rollout(x, s, steps, cfl=0.5)
+    loss = 0.5 * ((out[0] - tgt) ** 2).sum()
+    loss.backward()
+    grad = x.grad.detach()
+    peak = torch.cuda.max_memory_allocated()
+    dts = []
+    Uc = torch.from_numpy(U0).cuda()
+    for _ in range(steps):
+        dts.append(s.step(Uc, 0.0, 0.5, return_dt=True))
+    assert abs(float(loss) - 0.5 * float(((Uc[0] - tgt) ** 2).sum())) <= 1e-12 * float(loss)
+
+    xs = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(xs, xs)
+    bump = np.exp(-((X - centre[0]) ** 2 + (Y - centre[1]) ** 2) / 2.0)
+    eps = 1e-8
+    A1, A2, A3, B1, B2, B3 = (torch.empty_like(Uc) for _ in range(6))
+
+    def pair_losses(dd):
+        """Central difference of the loss along dd, the +eps and -eps runs
+        advanced stage by stage side by side with the reference dt sequence;
+        False if any stage's selections differ between the two runs."""
+        nonlocal A3, B3
+        up, um = x.detach() + eps * dd, x.detach() - eps * dd
+        same = True
+        for dt in dts:
+            for st, (ps, po, ms, mo) in enumerate(((up, A1, um, B1), (A1, A2, B1, B2),
+                                                   (A2, A3, B2, B3)), start=1):
+                if same and not torch.equal(s.selection(ps), s.selection(ms)):
+                    same = False
+                s.stage(st, up, ps, po, dt)
+                s.stage(st, um, ms, mo, dt)
+            up, A3 = A3, up
+            um, B3 = B3, um
+        lp = 0.5 * float(((up[0] - tgt) ** 2).sum())
+        lm = 0.5 * float(((um[0] - tgt) ** 2).sum())
+        return (lp - lm) / (2 * eps), same
+
+    used, left_out = 0, 0
+    for k in range(8):
+        d = torch.from_numpy(smooth_dir(U0, 40 + k) * bump[None]).cuda()
+        fd, same = pair_losses(d)
+        ad = float((grad * d).sum())
+        rel = abs(fd - ad) / abs(fd)
+        print(f"vortex 512^2, 200 steps, direction {k}: fd {fd:.10e} adjoint {ad:.10e} "
+              f"rel {rel:.2e} {'' if same else '(selections differ between +-eps: left out)'}")
+        if not same:
+            left_out += 1
+            continue
+        used += 1
+        assert rel <= 1e-6, (k, fd, ad)
+    print(f"vortex 512^2 x 200 steps: {used} directions checked, {left_out} left out; "
+          f"peak torch memory {peak / 2**30:.2f} GiB (checkpoints {steps} x "
+          f"{U0.nbytes / 2**20:.0f} MiB)")
+    assert used >= 6
+    s.check_status()
