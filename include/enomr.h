@@ -220,15 +220,17 @@ ENOMR_API enomr_status enomr_get_status(enomr_ctx *ctx);
 /*
  * enomr_set_staging -- how the 2D Euler sweeps bring a tile of cells (with
  * its g-cell halos, Sec. 2.1) into shared memory:
- *   ENOMR_STAGING_AUTO  (default) the Tensor Memory Accelerator where the
- *                       state allows it (nx even, U 16-byte aligned, no
- *                       boundary sides or body force), else plain loads;
+ *   ENOMR_STAGING_AUTO  (default) where the state allows TMA (nx even, U
+ *                       16-byte aligned, no boundary sides or body force):
+ *                       the column (y) sweep by TMA, the row (x) sweep by
+ *                       TMA from order 15 and with plain loads below (the
+ *                       faster of the two on GB300); otherwise plain loads;
  *   ENOMR_STAGING_LOADS plain coalesced loads by the CTA's threads;
  *   ENOMR_STAGING_TMA   the TMA path only: calls whose state does not allow
  *                       it return ENOMR_EINVAL.
  * The TMA sweeps are persistent (one CTA per resident slot, a two-slot ring
  * of tile copies per CTA, the next tile's copy in flight during this
- * tile's arithmetic); both stagings give the same results bit for bit.
+ * tile's arithmetic); all stagings give the same results bit for bit.
  * Host-only setting, no synchronisation.
  */
 enum { ENOMR_STAGING_AUTO = 0, ENOMR_STAGING_LOADS = 1, ENOMR_STAGING_TMA = 2 };
@@ -245,6 +247,9 @@ ENOMR_API enomr_status enomr_set_staging(enomr_ctx *ctx, int mode);
  *                         few tiles in sequence;
  *   ENOMR_OCCUPANCY_AUTO  (default) LOW when the x sweep has fewer tiles
  *                         than two waves of the HIGH instance, else HIGH.
+ * On smooth data, where every interface takes the long path, LOW with TMA
+ * staging is the fastest instance (about 4 % on a 4096^2 vortex); on
+ * piecewise-constant data HIGH is (LOW is 40 % slower there).
  * Same results bit for bit.  Host-only setting, no synchronisation.
  */
 enum { ENOMR_OCCUPANCY_AUTO = 0, ENOMR_OCCUPANCY_HIGH = 1, ENOMR_OCCUPANCY_LOW = 2 };

@@ -587,6 +587,12 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
                      state_map(c, U, 1, &my);
     if (c->staging == ENOMR_STAGING_TMA && !tma) return ENOMR_EINVAL;
     const bool low = low_occupancy(c);
+    // Automatic staging, per sweep (measured on GB300, 4096^2 Riemann and
+    // vortex states): the column sweep is faster with TMA at every order (its
+    // tile then has no bank conflicts); the row sweep loads its rows with
+    // plain coalesced loads up to order 13 and is faster with TMA from 15 on.
+    const bool tma_x = tma && (c->staging == ENOMR_STAGING_TMA || c->order >= 15);
+    const bool tma_y = tma;
     SweepArgs ax = sweep_args(c, U, false);
     ax.sel = sel;
     ax.ft_out = ft;
@@ -594,9 +600,9 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     ax.epi.out = c->D;
     ax.t_coef = t_coef;
     prof_start(c, 1);
-    cudaError_t e = ext   ? by_order<E2XEF>(c->order, ax, low, c->stream)
-                    : tma ? by_order<E2XTF>(c->order, mx, ax, low, c->stream)
-                          : by_order<E2XF>(c->order, ax, low, c->stream);
+    cudaError_t e = ext     ? by_order<E2XEF>(c->order, ax, low, c->stream)
+                    : tma_x ? by_order<E2XTF>(c->order, mx, ax, low, c->stream)
+                            : by_order<E2XF>(c->order, ax, low, c->stream);
     prof_stop(c, 1);
     CU_TRY(e);
     SweepArgs ay = sweep_args(c, U, true);
@@ -606,9 +612,9 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     ay.epi.Dprev = c->D;
     ay.t_coef = t_coef;
     prof_start(c, 2);
-    e = ext   ? by_order<E2YEF>(c->order, ay, low, c->stream)
-        : tma ? by_order<E2YTF>(c->order, my, ay, low, c->stream)
-              : by_order<E2YF>(c->order, ay, low, c->stream);
+    e = ext     ? by_order<E2YEF>(c->order, ay, low, c->stream)
+        : tma_y ? by_order<E2YTF>(c->order, my, ay, low, c->stream)
+                : by_order<E2YF>(c->order, ay, low, c->stream);
     prof_stop(c, 2);
     return cu(e);
 }

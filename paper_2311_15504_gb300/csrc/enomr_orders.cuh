@@ -147,15 +147,17 @@ namespace enomr {
 template <int R> cudaError_t launch_euler2d_x_tma(const CUtensorMap &map, const SweepArgs &a,
                                                   bool low, cudaStream_t s)
 {
-    return low ? launch_sweep_tma<R, 0, X_TP, X_NL, SWEEP_LOW_CTAS>(map, a, s)
-               : launch_sweep_tma<R, 0, X_TP, X_NL, TmaCtas<R, 0, X_TP, X_NL>::value>(map, a, s);
+    return low ? launch_sweep_tma<R, 0, X_TP, X_NL, SWEEP_LOW_CTAS, true>(map, a, s)
+               : launch_sweep_tma<R, 0, X_TP, X_NL, TmaCtas<R, 0, X_TP, X_NL>::value, false>(map, a,
+                                                                                          s);
 }
 
 template <int R> cudaError_t launch_euler2d_y_tma(const CUtensorMap &map, const SweepArgs &a,
                                                   bool low, cudaStream_t s)
 {
-    return low ? launch_sweep_tma<R, 1, Y_TP, Y_NL, SWEEP_LOW_CTAS>(map, a, s)
-               : launch_sweep_tma<R, 1, Y_TP, Y_NL, TmaCtas<R, 1, Y_TP, Y_NL>::value>(map, a, s);
+    return low ? launch_sweep_tma<R, 1, Y_TP, Y_NL, SWEEP_LOW_CTAS, true>(map, a, s)
+               : launch_sweep_tma<R, 1, Y_TP, Y_NL, TmaCtas<R, 1, Y_TP, Y_NL>::value, false>(map, a,
+                                                                                          s);
 }
 
 template cudaError_t launch_euler2d_x_tma<ENOMR_R>(const CUtensorMap &, const SweepArgs &, bool,

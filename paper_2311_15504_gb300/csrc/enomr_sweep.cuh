@@ -51,13 +51,15 @@ struct SweepSmem {
 // View of a tile's shared memory used by sweep_tile and interface_flux.
 // U(q, line, s): state component q (line order: rho, m_n, [m_t], E) of
 // staged cell s of tile line `line`; F: its normal flux; P: sqrt(rho), u_n,
-// u_t, H; Fh(q, line, p): flux of interface p.  kLoads: the staging phase
+// u_t, H (views with kStagedP; the others evaluate them where needed);
+// Fh(q, line, p): flux of interface p.  kLoads: the staging phase
 // loads the cells from global memory itself (true here); a view whose
 // cells are already in shared memory (the TMA ring of enomr_tma.cuh) reads
 // them in place.
 template <int R, int C, int DIR, int TP, int NL>
 struct ClassicTile {
     static constexpr bool kLoads = true;
+    static constexpr bool kStagedP = true;  // P staged per cell (else evaluated on demand)
     SweepSmem<R, C, TP, NL> &sm;
     __device__ __forceinline__ double &U(int q, int line, int s) const { return sm.sU[q][line][s]; }
     __device__ __forceinline__ double &F(int q, int line, int s) const { return sm.sF[q][line][s]; }
@@ -160,9 +162,27 @@ __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0,
 #pragma unroll
     for (int q = 0; q < C; ++q)
         eqLR = eqLR && (__double_as_longlong(t.U(q, line, sl)) == __double_as_longlong(t.U(q, line, sr)));
-    const RoeFace rf = roe_face(eqLR, t.P(0, line, sl), t.P(1, line, sl), t.P(2, line, sl),
-                                t.P(3, line, sl), t.P(0, line, sr), t.P(1, line, sr),
-                                t.P(2, line, sr), t.P(3, line, sr), C == 4, A.gm1, A.inv_gm1);
+    // sqrt(rho), u_n, u_t, H of the two centre cells: staged per cell, or
+    // (views without them) evaluated here by the same operations
+    const RoeFace rf = [&]() {
+        if constexpr (Tile::kStagedP) {
+            return roe_face(eqLR, t.P(0, line, sl), t.P(1, line, sl), t.P(2, line, sl),
+                            t.P(3, line, sl), t.P(0, line, sr), t.P(1, line, sr),
+                            t.P(2, line, sr), t.P(3, line, sr), C == 4, A.gm1, A.inv_gm1);
+        } else {
+            const StagedCell<C> cl = stage_cell<C>(t.U(0, line, sl), t.U(1, line, sl),
+                                                   (C == 4) ? t.U(2, line, sl) : 0.0,
+                                                   t.U(C - 1, line, sl), A.gm1);
+            if (eqLR)
+                return roe_face(true, cl.sq, cl.un, cl.ut, cl.H, cl.sq, cl.un, cl.ut, cl.H, C == 4,
+                                A.gm1, A.inv_gm1);
+            const StagedCell<C> cr = stage_cell<C>(t.U(0, line, sr), t.U(1, line, sr),
+                                                   (C == 4) ? t.U(2, line, sr) : 0.0,
+                                                   t.U(C - 1, line, sr), A.gm1);
+            return roe_face(false, cl.sq, cl.un, cl.ut, cl.H, cr.sq, cr.un, cr.ut, cr.H, C == 4,
+                            A.gm1, A.inv_gm1);
+        }
+    }();
     if (valid && !positive(rf.c2)) atomicOr(A.status, ST_NONPHYS_ROE);
     const double uh = rf.uh, vh = rf.vh, Hh = rf.Hh, hq = rf.hq, cs = rf.cs, kap = rf.kap,
                  c2g = rf.c2g, b1 = rf.b1;
@@ -290,6 +310,17 @@ __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0,
         for (int q = 0; q < C; ++q) t.Fh(q, line, p) = Fh[q];
 }
 
+// A flat interface that is not on one state (or whose per-field values are
+// recorded): projection of its centre cells (interface_flux, FLATP).  Not
+// inlined, so that it stays a branch of its caller.
+template <int R, int C, int DIR, int TP, int NL, class Tile>
+__device__ __noinline__ void flat_projection(const SweepArgs &A, long long x0, long long l0,
+                                             const double *sA, const Tile &t, int p, int line,
+                                             bool e2)
+{
+    interface_flux<R, C, DIR, TP, NL, true>(A, x0, l0, sA, t, p, line, true, e2);
+}
+
 // One tile: NL lines x TP interfaces starting at interface x0 of line l0.
 // All threads of the CTA must call it; it ends after its epilogue.
 // EXT: the 2D sweep with boundary sides and a body force (SweepArgs'
@@ -407,10 +438,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
                     atomicOr(A.status, ST_NONPHYS_CELL);
 #pragma unroll
                 for (int q = 0; q < C; ++q) t.F(q, line, s) = sc_.F[q];
-                t.P(0, line, s) = sc_.sq;
-                t.P(1, line, s) = sc_.un;
-                t.P(2, line, s) = sc_.ut;
-                t.P(3, line, s) = sc_.H;
+                if constexpr (Tile::kStagedP) {
+                    t.P(0, line, s) = sc_.sq;
+                    t.P(1, line, s) = sc_.un;
+                    t.P(2, line, s) = sc_.ut;
+                    t.P(3, line, s) = sc_.H;
+                }
             }
         }
     }
@@ -433,7 +466,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
 #pragma unroll
             for (int q = 0; q < C; ++q) t.F(q, line, s) = t.F(q, lr, sr_);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) t.P(q, line, s) = t.P(q, lr, sr_);
+            for (int q = 0; q < 4; ++q)
+                if constexpr (Tile::kStagedP) t.P(q, line, s) = t.P(q, lr, sr_);
         }
     }
     __syncthreads();
@@ -471,8 +505,18 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
         const bool plus_flat = (e0 && e1) || (e2 && e3);   // centre cell k-1
         const bool minus_flat = (e3 && e4) || (e1 && e2);  // centre cell k (mirrored)
         const bool flat = plus_flat && minus_flat;
-        if (valid && flat)
-            interface_flux<R, C, DIR, TP, NL, true>(A, x0, l0, sA, t, p, line, true, e2);
+        // One-state flat interfaces (most of a piecewise-constant grid) take
+        // the cell's flux inline; the few other flat ones project their centre
+        // cells in a separate, non-inlined function, so that the compiler
+        // cannot if-convert that FP64 code into this per-thread path (where
+        // every one-state lane would issue it predicated off and hold the
+        // FP64 pipe for nothing).
+        if (valid && flat) {
+            if (e2 && !A.ft_out)
+                interface_flux<R, C, DIR, TP, NL, true>(A, x0, l0, sA, t, p, line, true, true);
+            else
+                flat_projection<R, C, DIR, TP, NL>(A, x0, l0, sA, t, p, line, e2);
+        }
         // append the other valid interfaces, in lane order within each warp
         const unsigned need = __ballot_sync(FULL, valid && !flat);
         if (need) {

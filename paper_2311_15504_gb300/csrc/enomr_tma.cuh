@@ -29,7 +29,7 @@
 
 namespace enomr {
 
-template <int R, int C, int DIR, int TP, int NL>
+template <int R, int C, int DIR, int TP, int NL, bool SP = false>
 struct TmaSmem {
     static constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
     static constexpr int S = TP + 2 * g - 1, NS = NL * S;
@@ -39,7 +39,7 @@ struct TmaSmem {
     static_assert((C * RAWN * 8) % 128 == 0, "ring slots must stay 128-byte aligned");
     double raw[2][C * RAWN];  // ring of tile copies, global component order
     double sF[C * NS];
-    double sP[4 * NS];  // sqrt(rho), u_n, u_t, H
+    double sP[SP ? 4 * NS : 1];  // sqrt(rho), u_n, u_t, H (SP: staged per cell)
     union {
         double sFh[C * NL * TP];
         unsigned short rep[NS];
@@ -58,10 +58,16 @@ struct TmaSmem {
 // Tile view over the ring slot holding the current tile (u: the slot plus
 // the row offset of the x sweep).  State components are mapped from line
 // order (rho, m_n, m_t, E) to the global order of the copy.
-template <int R, int C, int DIR, int TP, int NL>
+template <int R, int C, int DIR, int TP, int NL, bool SP = false>
 struct TmaTile {
-    using SM = TmaSmem<R, C, DIR, TP, NL>;
+    using SM = TmaSmem<R, C, DIR, TP, NL, SP>;
     static constexpr bool kLoads = false;
+    // SP false: sqrt(rho), u_n, u_t, H are evaluated where an interface needs
+    // them (the two centre cells of an interface that is not flat on one
+    // state), not staged: 9 KB less shared memory per tile and no staging
+    // stores, for a little more FP64 work on the long path.  SP true: staged
+    // per cell, as the loading sweeps do.
+    static constexpr bool kStagedP = SP;
     static constexpr int S = SM::S, BW = SM::BW, RAWN = SM::RAWN;
     SM &sm;
     double *u;
@@ -82,7 +88,10 @@ struct TmaTile {
         return u[gq(q) * RAWN + ri(line, s)];
     }
     __device__ __forceinline__ double &F(int q, int line, int s) const { return sm.sF[q * SM::NS + ci(line, s)]; }
-    __device__ __forceinline__ double &P(int q, int line, int s) const { return sm.sP[q * SM::NS + ci(line, s)]; }
+    __device__ __forceinline__ double &P(int q, int line, int s) const
+    {
+        return sm.sP[SP ? q * SM::NS + ci(line, s) : 0];
+    }
     __device__ __forceinline__ double &Fh(int q, int line, int p) const
     {
         return sm.sFh[q * NL * TP + ((DIR == 0) ? line * TP + p : p * NL + line)];
@@ -182,12 +191,12 @@ struct TmaGeom {
 // Persistent TMA sweep over ntiles tiles (x sweep: segment-fastest order
 // along the rows; y sweep: column-group-fastest, so that the concurrently
 // processed tiles of a wave share DRAM pages).
-template <int R, int DIR, int TP, int NL, int MINB>
+template <int R, int DIR, int TP, int NL, int MINB, bool SP>
 __global__ void __launch_bounds__(TP *NL, MINB)
     k_sweep_tma(const __grid_constant__ CUtensorMap map, SweepArgs A, long long ntiles)
 {
     constexpr int C = 4;
-    using SM = TmaSmem<R, C, DIR, TP, NL>;
+    using SM = TmaSmem<R, C, DIR, TP, NL, SP>;
     using G = TmaGeom<R, DIR, TP, NL>;
     constexpr int g = SM::g, S = SM::S, NS = SM::NS, RAWN = SM::RAWN, NT = TP * NL;
     constexpr unsigned BYTES = (unsigned)(sizeof(double) * C * RAWN);
@@ -256,7 +265,7 @@ __global__ void __launch_bounds__(TP *NL, MINB)
         tile_of(t, x0, l0);
         double *base = sm.raw[slot];
         if (DIR == 0) base += (x0 - g) & 1;  // the copy started at the even x at or below x0 - g
-        const TmaTile<R, C, DIR, TP, NL> tile{sm, base};
+        const TmaTile<R, C, DIR, TP, NL, SP> tile{sm, base};
         // ghost cells and lines past the last one: plain loads (the ends of
         // the lines only)
         if (x0 - g < 0 || x0 - g + S > nlen || l0 + NL > nlines) {
@@ -276,7 +285,7 @@ __global__ void __launch_bounds__(TP *NL, MINB)
                     const long long gi = (DIR == 0) ? Lc * nx + cell : cell * nx + Lc;
 #pragma unroll
                     for (int q = 0; q < C; ++q)
-                        base[q * RAWN + TmaTile<R, C, DIR, TP, NL>::ri(line, s)] =
+                        base[q * RAWN + TmaTile<R, C, DIR, TP, NL, SP>::ri(line, s)] =
                             A.U[q * ncell + gi];
                 }
             }
@@ -289,10 +298,10 @@ __global__ void __launch_bounds__(TP *NL, MINB)
 // Host launcher: a persistent grid of (SMs x resident CTAs) CTAs, at most
 // one per tile.  map: tensor map of the state U of a (tiled, 3D: {nx, ny, 4})
 // with this sweep's box.
-template <int R, int DIR, int TP, int NL, int MINB>
+template <int R, int DIR, int TP, int NL, int MINB, bool SP>
 cudaError_t launch_sweep_tma(const CUtensorMap &map, const SweepArgs &a, cudaStream_t s)
 {
-    using SM = TmaSmem<R, 4, DIR, TP, NL>;
+    using SM = TmaSmem<R, 4, DIR, TP, NL, SP>;
     using G = TmaGeom<R, DIR, TP, NL>;
     constexpr int kMaxDev = 64;
     static int ctas[kMaxDev] = {}, sms[kMaxDev] = {};
@@ -300,7 +309,7 @@ cudaError_t launch_sweep_tma(const CUtensorMap &map, const SweepArgs &a, cudaStr
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
-    auto k = k_sweep_tma<R, DIR, TP, NL, MINB>;
+    auto k = k_sweep_tma<R, DIR, TP, NL, MINB, SP>;
     if (ctas[dev] == 0) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM));
         if (e != cudaSuccess) return e;
