@@ -211,6 +211,24 @@ ENOMR_API enomr_status enomr_get_time(enomr_ctx *ctx, double *t);
  */
 ENOMR_API enomr_status enomr_debug_selection(enomr_ctx *ctx, const double *U, uint8_t *sel);
 
+/*
+ * enomr_stage_frozen -- one SSP-RK3 stage as enomr_stage(), with the discrete
+ *   choices of the right-hand side taken from the reference state Uref
+ *   instead of Us: the stencil or minmod branch of every interface, field
+ *   and side (Sec. 3.2) and the cell attaining every per-line alpha_k
+ *   (Eq. LF_Flux_Split read per field); every interface is evaluated in full
+ *   with those choices, so the result is a smooth function of Us.  This is
+ *   the map that enomr_step_vjp transposes: finite differences of it check
+ *   the adjoint at any horizon, where those of the plain step cross
+ *   selection changes.  With Uref = Us it equals enomr_stage to rounding
+ *   (the one-state flat interfaces' shortcut aside).  2D Euler without
+ *   boundary sides or body force only (else ENOMR_EINVAL); Uout must not
+ *   alias Us or Uref.  Uses the context's adjoint scratch.
+ */
+ENOMR_API enomr_status enomr_stage_frozen(enomr_ctx *ctx, int s, const double *Un,
+                                          const double *Us, double *Uout, double dt,
+                                          const double *Uref);
+
 /* enomr_get_status -- synchronise the stream, read and clear the device
  * status word: ENOMR_OK, ENOMR_ENONPHYS, or ENOMR_ETIMEOUT when a sweep's
  * bounded wait for a tile copy ran out (that launch stopped early and its

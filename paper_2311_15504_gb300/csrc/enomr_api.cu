@@ -254,6 +254,37 @@ __global__ void k_alpha_vjp(const double *U, long long nx, long long ny, double 
     atomicAdd(Ubar + (C - 1) * ncell + i, E_b);
 }
 
+// alpha_k of every line evaluated at a given cell of the line (the frozen
+// argmax cells of a reference state): |lambda_k(U_a)|, by the same helper
+// as k_alpha, so with the reference state itself the maxima come back bit
+// for bit.  One thread per (line, k); rows (x sweep) first, then columns.
+template <int C>
+__global__ void k_alpha_at(const double *U, long long nx, long long ny, double gm1, double gamma,
+                           const unsigned long long *ix, const unsigned long long *iy,
+                           double *ax, double *ay, int *status)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nl = (C == 4) ? ny + nx : ny;
+    if (t >= 3 * nl) return;
+    const long long line = t / 3;
+    const int k = (int)(t - 3 * line);
+    const bool ysw = line >= ny;
+    const unsigned long long a = ysw ? iy[3 * (line - ny) + k] : ix[3 * line + k];
+    double *out = ysw ? ay + 3 * (line - ny) + k : ax + 3 * line + k;
+    const long long nlen = ysw ? ny : nx;
+    if (a >= (unsigned long long)nlen) {  // no cell attained the maximum (non-finite state)
+        *out = __longlong_as_double(0x7ff8000000000000LL);
+        atomicOr(status, ST_NONPHYS_CELL);
+        return;
+    }
+    const long long ncell = nx * ny;
+    const long long i = ysw ? (long long)a * nx + (line - ny) : line * nx + (long long)a;
+    const CellWaves cw = cell_waves<C>(U[i], U[ncell + i], (C == 4) ? U[2 * ncell + i] : 0.0,
+                                       U[(C - 1) * ncell + i], gm1, gamma, status);
+    const double un = ysw ? cw.v : cw.u;
+    *out = (k == 0) ? fabs(__dsub_rn(un, cw.c)) : ((k == 1) ? fabs(un) : fabs(__dadd_rn(un, cw.c)));
+}
+
 // y = a x (+ y if acc)
 __global__ void k_axpy(long long n, double a, const double *x, double *y, int acc)
 {
@@ -515,6 +546,7 @@ static SweepArgs sweep_args(enomr_ctx *c, const double *U, bool ysweep)
     a.alpha = ysweep ? c->ay : c->ax;
     a.alpha_next = nullptr;
     a.sel = nullptr;
+    a.sel_in = nullptr;
     a.ft_out = nullptr;
     a.status = c->status;
     memset(&a.epi, 0, sizeof(a.epi));
@@ -550,7 +582,8 @@ static bool low_occupancy(const enomr_ctx *c)
 
 // Evaluate L(U) into the epilogue.  The alpha of U must be current.
 static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilogue &epi,
-                                      uint8_t *sel, double *ft = nullptr, double t_coef = 0.0)
+                                      uint8_t *sel, double *ft = nullptr, double t_coef = 0.0,
+                                      const uint8_t *sel_in = nullptr)
 {
     if (c->eq == ENOMR_ADVECTION || c->eq == ENOMR_BURGERS) {
         AdvArgs a;
@@ -595,6 +628,7 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     const bool tma_y = tma;
     SweepArgs ax = sweep_args(c, U, false);
     ax.sel = sel;
+    ax.sel_in = sel_in;
     ax.ft_out = ft;
     ax.epi.mode = EPI_STORE;
     ax.epi.out = c->D;
@@ -607,6 +641,7 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
     CU_TRY(e);
     SweepArgs ay = sweep_args(c, U, true);
     ay.sel = sel ? sel + 8LL * c->ny * (c->nx + 1) : nullptr;
+    ay.sel_in = sel_in ? sel_in + 8LL * c->ny * (c->nx + 1) : nullptr;
     ay.ft_out = ft ? ft + 4LL * c->ny * (c->nx + 1) : nullptr;
     ay.epi = epi;
     ay.epi.Dprev = c->D;
@@ -919,6 +954,57 @@ ENOMR_API enomr_status enomr_cfl_dt(enomr_ctx *c, const double *U, double cfl, d
     CU_TRY(cudaMemcpyAsync(dt_host, c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU_TRY(cudaStreamSynchronize(c->stream));
     return ENOMR_OK;
+}
+
+ENOMR_API enomr_status enomr_stage_frozen(enomr_ctx *c, int s, const double *Un,
+                                          const double *Us, double *Uout, double dt,
+                                          const double *Uref)
+{
+    if (!c || s < 1 || s > 3 || !Un || !Us || !Uout || !Uref || !(dt > 0.0)) return ENOMR_EINVAL;
+    if (c->eq != ENOMR_EULER || c->ndim != 2 || extended(c)) return ENOMR_EINVAL;
+    if (s == 1 && Us != Un) return ENOMR_EINVAL;
+    if ((const double *)Uout == Us || (const double *)Uout == Uref) return ENOMR_EINVAL;
+    if (s == 1 && (const double *)Uout == Un) return ENOMR_EINVAL;
+    CU_TRY(launch_set_dt(c->smax, 0.0, dt, c->dt, c->stream));
+    // the choices of Uref: its per-line alpha, the selections of its sweeps
+    // (into fsel[0]; the right-hand side goes to the stage scratch and is
+    // discarded) and the cells attaining each alpha
+    enomr_status st = compute_alpha(c, Uref, false);
+    if (st) return st;
+    Epilogue er;
+    memset(&er, 0, sizeof(er));
+    er.mode = EPI_STORE;
+    er.out = c->U2;
+    if ((st = rhs_with_epilogue(c, Uref, er, c->fsel[0]))) return st;
+    CU_TRY(cudaMemsetAsync(c->ix, 0xff, sizeof(unsigned long long) * 3 * c->ny, c->stream));
+    CU_TRY(cudaMemsetAsync(c->iy, 0xff, sizeof(unsigned long long) * 3 * c->nx, c->stream));
+    AlphaArgs aa;
+    memset(&aa, 0, sizeof(aa));
+    aa.U = Uref;
+    aa.nx = c->nx;
+    aa.ny = c->ny;
+    aa.gm1 = c->gamma - 1.0;
+    aa.gamma = c->gamma;
+    aa.ax = c->ax;
+    aa.ay = c->ay;
+    aa.status = c->status;
+    dim3 grid((unsigned)((c->nx + 31) / 32), (unsigned)((c->ny + 31) / 32));
+    k_alpha_argmax<4><<<grid, 256, 0, c->stream>>>(aa, c->ix, c->iy);
+    CU_TRY(cudaGetLastError());
+    // alpha of Us at those cells, then the stage with the frozen selections
+    const long long nl = c->ny + c->nx;
+    k_alpha_at<4><<<(unsigned)((3 * nl + 255) / 256), 256, 0, c->stream>>>(
+        Us, c->nx, c->ny, c->gamma - 1.0, c->gamma, c->ix, c->iy, c->ax, c->ay, c->status);
+    CU_TRY(cudaGetLastError());
+    Epilogue e;
+    memset(&e, 0, sizeof(e));
+    e.mode = EPI_STAGE;
+    e.c0 = RK_C0[s - 1];
+    e.c1 = RK_C1[s - 1];
+    e.dt_dev = c->dt;
+    e.Un = Un;
+    e.out = Uout;
+    return rhs_with_epilogue(c, Us, e, nullptr, nullptr, 0.0, c->fsel[0]);
 }
 
 ENOMR_API enomr_status enomr_debug_selection(enomr_ctx *c, const double *U, uint8_t *sel)

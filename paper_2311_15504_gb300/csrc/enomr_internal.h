@@ -57,6 +57,8 @@ struct SweepArgs {
     const double *alpha;   // [lines][3]: max|un-c|, max|un|, max|un+c|
     double *alpha_next;    // 1D only: accumulate the output state's alpha here, or nullptr
     uint8_t *sel;          // optional selection dump for this sweep
+    const uint8_t *sel_in; // optional forced selections (same layout): every
+                           // interface is evaluated in full with these choices
     double *ft_out;        // optional: f^+ + f^- per field and interface, [C][lines][nlen+1]
     int *status;
     Epilogue epi;

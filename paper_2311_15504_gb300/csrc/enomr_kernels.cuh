@@ -129,6 +129,26 @@ __device__ __forceinline__ double mr_value(const double *v, const double *sA, bo
     return val;
 }
 
+// Value of the ENO-MR reconstruction of window v with the choice given
+// (frozen): a tested stencil (table row), or a minmod outcome T, T+1, T+2;
+// the same operations as mr_value's evaluation of that choice.
+template <int R>
+__device__ __forceinline__ double mr_value_forced(const double *v, const double *sA, int sel)
+{
+    constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T, c = g - 1;
+    if (sel < T) {
+        const double *row = sA + sel * W;
+        double val = 0.0;
+#pragma unroll
+        for (int l = 0; l < W; ++l) val = fma(row[l], v[l], val);
+        return val;
+    }
+    double mm = 0.0;
+    if (sel == T) mm = -(v[c] - v[c + 1]);
+    if (sel == T + 1) mm = v[c] - v[c - 1];
+    return fma(0.5, mm, v[c]);
+}
+
 template <int R>
 __device__ __forceinline__ void load_a_table(double *sA, int tid, int nthreads)
 {

@@ -48,6 +48,10 @@ struct SweepSmem {
                   "staging arrays must fit in the storage they share");
 };
 
+// Largest partly filled last warp of a tile's long-path list that is
+// evaluated field-parallel (interface_flux, fsel).
+constexpr int LONG_TAIL = 16;
+
 // View of a tile's shared memory used by sweep_tile and interface_flux.
 // U(q, line, s): state component q (line order: rho, m_n, [m_t], E) of
 // staged cell s of tile line `line`; F: its normal flux; P: sqrt(rho), u_n,
@@ -119,10 +123,14 @@ __device__ __forceinline__ void side_cell(const SweepArgs &A, long long craw, lo
 // are bitwise equal), e2: its two centre states are bitwise equal.  The
 // long path (FLATP false) holds warp votes: all 32 lanes of the warp call
 // it together, lanes with valid == false only vote.
+// fsel >= 0 (long path, C = 4 only): field-parallel form; lanes 4i .. 4i+3
+// of the warp hold one interface and each evaluates field fsel = lane % 4
+// only (same operations as the loop over the fields); the four values meet
+// at the first lane by shuffles, which alone back-projects and stores.
 template <int R, int C, int DIR, int TP, int NL, bool FLATP, class Tile>
 __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0, long long l0,
                                                const double *sA, const Tile &t, int p, int line,
-                                               bool valid, bool e2)
+                                               bool valid, bool e2, int fsel = -1)
 {
     constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
     const long long nlen = (DIR == 0) ? A.nx : A.ny;
@@ -183,7 +191,7 @@ __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0,
                             A.gm1, A.inv_gm1);
         }
     }();
-    if (valid && !positive(rf.c2)) atomicOr(A.status, ST_NONPHYS_ROE);
+    if (valid && fsel <= 0 && !positive(rf.c2)) atomicOr(A.status, ST_NONPHYS_ROE);
     const double uh = rf.uh, vh = rf.vh, Hh = rf.Hh, hq = rf.hq, cs = rf.cs, kap = rf.kap,
                  c2g = rf.c2g, b1 = rf.b1;
 
@@ -273,6 +281,45 @@ __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0,
             }
             if (A.ft_out && valid) A.ft_out[(f * nlines + Lg) * (nlen + 1) + k] = fp + fm;
         }
+    } else if (C == 4 && fsel >= 0) {
+        const int f = fsel;
+        double l0c, l1c, alpha;
+        row(f, l0c, l1c, alpha);
+        double vp[W], vm[W];
+#pragma unroll
+        for (int j = 0; j < 2 * g; ++j) {
+            double w, q;
+            project(f, p + j, l0c, l1c, w, q);
+            if (j <= 2 * g - 2) vp[j] = fma(alpha, w, q);
+            if (j >= 1) vm[2 * g - 1 - j] = fma(-alpha, w, q);
+        }
+        int selp, selm;
+        double fp, fm;
+        if (A.sel_in) {
+            const long long NI = nlen + 1;
+            selp = A.sel_in[((0 * C + f) * nlines + Lg) * NI + k];
+            selm = A.sel_in[((1 * C + f) * nlines + Lg) * NI + k];
+            fp = mr_value_forced<R>(vp, sA, selp);
+            fm = mr_value_forced<R>(vm, sA, selm);
+        } else {
+            fp = mr_value<R>(vp, sA, valid, selp);
+            fm = mr_value<R>(vm, sA, valid, selm);
+        }
+        const double ft = fp + fm;
+        if (A.sel && valid) {
+            const long long NI = nlen + 1;
+            A.sel[((0 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selp;
+            A.sel[((1 * C + f) * nlines + Lg) * NI + k] = (uint8_t)selm;
+        }
+        if (A.ft_out && valid) A.ft_out[(f * nlines + Lg) * (nlen + 1) + k] = ft;
+        const int first = (threadIdx.x & 31) & ~3;
+        double fts[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fts[q] = __shfl_sync(FULL, ft, first + q);
+        if constexpr (C == 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) accumulate(q, fts[q]);
+        }
     } else {
 #pragma unroll 1
         for (int f = 0; f < C; ++f) {
@@ -287,8 +334,20 @@ __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0,
                 if (j >= 1) vm[2 * g - 1 - j] = fma(-alpha, w, q);  // cell k-l,   l = g-j
             }
             int selp, selm;
-            const double fp = mr_value<R>(vp, sA, valid, selp);
-            const double fm = mr_value<R>(vm, sA, valid, selm);
+            double fp, fm;
+            if (A.sel_in) {
+                // frozen choices (forced per interface): no warp votes here,
+                // and the caller gives a uniform A.sel_in to the whole warp
+                const long long NI = nlen + 1;
+                const long long kk = valid ? k : 0, Lk = valid ? Lg : 0;
+                selp = A.sel_in[((0 * C + f) * nlines + Lk) * NI + kk];
+                selm = A.sel_in[((1 * C + f) * nlines + Lk) * NI + kk];
+                fp = mr_value_forced<R>(vp, sA, selp);
+                fm = mr_value_forced<R>(vm, sA, selm);
+            } else {
+                fp = mr_value<R>(vp, sA, valid, selp);
+                fm = mr_value<R>(vm, sA, valid, selm);
+            }
             accumulate(f, fp + fm);
             if (A.sel && valid) {
                 const long long NI = nlen + 1;
@@ -304,8 +363,8 @@ __device__ __forceinline__ void interface_flux(const SweepArgs &A, long long x0,
     if (C == 4) Fh[2] = fma(vh, Fh[0], ph2);
     Fh[C - 1] = fma(Hh, acc_s, fma(uh * cs, acc_d, fma(hq, ph1, vh * ph2)));
     // a lane without an interface of its own (it only votes) must not store
-    // over the owner's slot
-    if (valid)
+    // over the owner's slot; in the field-parallel form the first lane stores
+    if (valid && fsel <= 0)
 #pragma unroll
         for (int q = 0; q < C; ++q) t.Fh(q, line, p) = Fh[q];
 }
@@ -321,11 +380,42 @@ __device__ __noinline__ void flat_projection(const SweepArgs &A, long long x0, l
     interface_flux<R, C, DIR, TP, NL, true>(A, x0, l0, sA, t, p, line, true, e2);
 }
 
+// Long path of one interface per lane; all 32 lanes call it together.  Not
+// inlined, like the other FP64-heavy paths of a tile: kept out of line, its
+// code cannot be merged (if-converted) into the per-thread phases of the
+// tile, where most lanes would issue it predicated off.
+template <int R, int C, int DIR, int TP, int NL, class Tile>
+__device__ __noinline__ void long_path(const SweepArgs &A, long long x0, long long l0,
+                                       const double *sA, const Tile &t, int p, int line,
+                                       bool valid)
+{
+    interface_flux<R, C, DIR, TP, NL, false>(A, x0, l0, sA, t, p, line, valid, false);
+}
+
+// Field-parallel long path of one interface (fsel = lane % 4); all 32 lanes
+// call it together.  Not inlined: a second inlined copy of the long path
+// would double the sweeps' register spills.
+template <int R, int C, int DIR, int TP, int NL, class Tile>
+__device__ __noinline__ void long_tail(const SweepArgs &A, long long x0, long long l0,
+                                       const double *sA, const Tile &t, int p, int line,
+                                       bool valid, int fsel)
+{
+    interface_flux<R, C, DIR, TP, NL, false>(A, x0, l0, sA, t, p, line, valid, false, fsel);
+}
+
 // One tile: NL lines x TP interfaces starting at interface x0 of line l0.
 // All threads of the CTA must call it; it ends after its epilogue.
 // EXT: the 2D sweep with boundary sides and a body force (SweepArgs'
 // side_lo, side_hi, ..., src set); the plain instances leave them unread.
-template <int R, int C, int DIR, int TP, int NL, bool EXT = false, class Tile>
+// LM: form of the long path.  LONG_SPLIT (default): whole warps out of line
+// (long_path) and a partly filled last warp field-parallel (long_tail).
+// LONG_INLINE: every warp inline, interface-parallel -- the form measured
+// fastest for the plain-load row sweep of piecewise-constant grids, whose
+// code generation is sensitive to what surrounds its per-thread flat path.
+enum : int { LONG_INLINE = 0, LONG_SPLIT = 1 };
+
+template <int R, int C, int DIR, int TP, int NL, bool EXT = false, int LM = LONG_SPLIT,
+          class Tile>
 __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, long long l0,
                                            const double *sA, const Tile &t)
 {
@@ -504,7 +594,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
                    e3 = same(sr, sr + 1), e4 = same(sr + 1, sr + 2);
         const bool plus_flat = (e0 && e1) || (e2 && e3);   // centre cell k-1
         const bool minus_flat = (e3 && e4) || (e1 && e2);  // centre cell k (mirrored)
-        const bool flat = plus_flat && minus_flat;
+        // with forced (frozen) choices every interface is evaluated in full
+        const bool flat = plus_flat && minus_flat && !A.sel_in;
         // One-state flat interfaces (most of a piecewise-constant grid) take
         // the cell's flux inline; the few other flat ones project their centre
         // cells in a separate, non-inlined function, so that the compiler
@@ -528,12 +619,44 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
     }
     __syncthreads();
     {
+        // Whole warps of 32 interfaces each; a last, partly filled warp of at
+        // most LONG_TAIL interfaces is evaluated field-parallel instead (four
+        // lanes per interface, one field each, eight interfaces per warp):
+        // the FP64 pipe is charged per warp instruction, and one field costs
+        // about a third of a whole interface, so a few interfaces -- the
+        // typical count of a tile crossing a front -- take a third of the
+        // pipe time and of the latency.
         const int n = t.nlist();
-        for (int base = tid & ~31; base < n; base += NT) {
+        int nip = n;
+        if constexpr (LM == LONG_INLINE) {
+            for (int base = tid & ~31; base < n; base += NT) {
+                const int j = base + (tid & 31);
+                const bool act = j < n;
+                const int e = t.list()[act ? j : base];
+                interface_flux<R, C, DIR, TP, NL, false>(A, x0, l0, sA, t, e % TP, e / TP, act,
+                                                        false);
+            }
+            nip = -1;  // done
+        } else if constexpr (C == 4) {
+            const int r = n & 31;
+            if (r > 0 && r <= LONG_TAIL) nip = n - r;
+        }
+        for (int base = tid & ~31; base < nip; base += NT) {
             const int j = base + (tid & 31);
-            const bool act = j < n;
+            const bool act = j < nip;
             const int e = t.list()[act ? j : base];
-            interface_flux<R, C, DIR, TP, NL, false>(A, x0, l0, sA, t, e % TP, e / TP, act, false);
+            long_path<R, C, DIR, TP, NL>(A, x0, l0, sA, t, e % TP, e / TP, act);
+        }
+        if (C == 4 && nip >= 0 && nip < n) {
+            // the warps without a whole-warp chunk take the tail's chunks
+            constexpr int NW = NT / 32;
+            const int w0 = (nip >> 5) % NW, nchunk = (n - nip + 7) >> 3;
+            for (int c = ((tid >> 5) - w0 + NW) % NW; c < nchunk; c += NW) {
+                const int j = nip + c * 8 + (lane >> 2);
+                const bool act = j < n;
+                const int e = t.list()[act ? j : nip];
+                long_tail<R, C, DIR, TP, NL>(A, x0, l0, sA, t, e % TP, e / TP, act, lane & 3);
+            }
         }
     }
     __syncthreads();
@@ -615,7 +738,7 @@ constexpr int SWEEP_THREADS_PER_SM = SWEEP_HIGH_THREADS_PER_SM;
 constexpr int SWEEP_LOW_CTAS = 2;
 
 template <int R, int C, int DIR, int TP, int NL, bool EXT = false,
-          int MINB = SWEEP_THREADS_PER_SM / (TP * NL)>
+          int MINB = SWEEP_THREADS_PER_SM / (TP * NL), int LM = LONG_SPLIT>
 __global__ void __launch_bounds__(TP *NL, MINB) k_sweep(SweepArgs A)
 {
     constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
@@ -624,7 +747,7 @@ __global__ void __launch_bounds__(TP *NL, MINB) k_sweep(SweepArgs A)
     load_a_table<R>(sA, threadIdx.x, TP * NL);
     const long long x0 = (long long)((DIR == 0) ? blockIdx.x : blockIdx.y) * (TP - 1);
     const long long l0 = (long long)((DIR == 0) ? blockIdx.y : blockIdx.x) * NL;
-    sweep_tile<R, C, DIR, TP, NL, EXT>(A, x0, l0, sA, ClassicTile<R, C, DIR, TP, NL>{sm});
+    sweep_tile<R, C, DIR, TP, NL, EXT, LM>(A, x0, l0, sA, ClassicTile<R, C, DIR, TP, NL>{sm});
 }
 
 // ---------------------------------------------------------------------------
@@ -657,6 +780,7 @@ __global__ void __launch_bounds__(TP) k_batch_stage(BatchArgs B)
         A.alpha = B.alpha + 3 * pr;
         A.alpha_next = B.alpha_next ? B.alpha_next + 3 * pr : nullptr;
         A.sel = nullptr;
+        A.sel_in = nullptr;
         A.ft_out = nullptr;
         A.status = B.status;
         A.epi.mode = EPI_STAGE;

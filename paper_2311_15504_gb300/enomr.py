@@ -74,6 +74,7 @@ _SIGS = {
     "enomr_set_time": (_I, [_P, _D]),
     "enomr_get_time": (_I, [_P, ctypes.POINTER(_D)]),
     "enomr_set_staging": (_I, [_P, _I]),
+    "enomr_stage_frozen": (_I, [_P, _I, _P, _P, _P, _D, _P]),
     "enomr_set_occupancy": (_I, [_P, _I]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -175,6 +176,15 @@ class Solver:
         self._stream()
         _check(_lib.enomr_stage(self._ctx, s, self._state(Un), self._state(Us),
                                 self._state(out, "out"), float(dt)), "enomr_stage")
+        return out
+
+    def stage_frozen(self, s, Un, Us, out, dt, Uref):
+        """Stage s with the discrete choices (stencils, minmod branches, alpha
+        argmax cells) of the reference state Uref (enomr_stage_frozen)."""
+        self._stream()
+        _check(_lib.enomr_stage_frozen(self._ctx, s, self._state(Un), self._state(Us),
+                                       self._state(out, "out"), float(dt),
+                                       self._state(Uref, "Uref")), "enomr_stage_frozen")
         return out
 
     def step(self, U, dt=0.0, cfl=0.5, return_dt=False):
