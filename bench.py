@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--paper-runs", action="store_true",
                     help="also time the paper's 2D problems as whole runs (about 2.5 min)")
+    ap.add_argument("--occupancy", choices=["auto", "high", "low"], default="auto",
+                    help="sweep instance of the paper's 2D runs (enomr_set_occupancy)")
     ap.add_argument("--only", choices=["adjoint", "batched", "vortex", "paper"], default=None,
                     help="run one secondary measurement alone (profiling aid)")
     return ap.parse_args()
@@ -266,7 +268,8 @@ def batched_gain(enomr, workloads, dev, a, nprob=4096, order=9, reps=5):
     sizes, Us, hs = workloads.riemann_batch(nprob, seed=0)
     B = enomr.Batch(sizes, hs, order=order, bc=enomr.TRANSMISSIVE, device=dev)
     Ub = B.pack(Us)
-    tile, grid = B.autotune(Ub, reps=2)
+    B.autotune(Ub, reps=2)
+    tile, grid, per_item = B.config()
     cells = int(sizes.sum())
 
     def timed(graph):
@@ -334,7 +337,8 @@ def batched_gain(enomr, workloads, dev, a, nprob=4096, order=9, reps=5):
     return {"workload": f"{nprob} 1D Euler Riemann problems, sizes log-uniform [128, 8192] "
                         f"({cells} cells), order {order}, transmissive, CFL {a.cfl}",
             "batched": {"value": cells * 3 / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
-                        "tile": tile, "grid": grid, "launches_per_step": 5},
+                        "tile": tile, "grid": grid, "tiles_per_item": per_item,
+                        "launches_per_step": 5},
             "per_problem_serial": {"value": cells * 3 / (ms_p * 1e-3), "unit": UNIT,
                                    "ms_per_step": ms_p, "launches_per_step": 7 * nprob,
                                    "form": "one stream, one CUDA graph"},
@@ -470,7 +474,8 @@ def scalar_work(order, sel, n, staged_ops):
     return w
 
 
-def paper_run(enomr, dev, name, U0, dx, dy, order, sides, gravity, gamma, cfl, t_end):
+def paper_run(enomr, dev, name, U0, dx, dy, order, sides, gravity, gamma, cfl, t_end,
+              occupancy="auto"):
     """One of the paper's 2D problems from t = 0 to t_end with CFL steps
     (each step reads its dt back to the host); host-timed whole run.  A run
     that turns non-physical stops and says so."""
@@ -482,6 +487,8 @@ def paper_run(enomr, dev, name, U0, dx, dy, order, sides, gravity, gamma, cfl, t
         s.set_sides(sides)
     if gravity != (0.0, 0.0):
         s.set_body_force(*gravity)
+    s.set_occupancy({"auto": enomr.OCCUPANCY_AUTO, "high": enomr.OCCUPANCY_HIGH,
+                     "low": enomr.OCCUPANCY_LOW}[occupancy])
     U = torch.from_numpy(U0).to(dev)
     s.step(U.clone(), 1e-9)  # warm-up
     s.time = 0.0
@@ -505,6 +512,7 @@ def paper_run(enomr, dev, name, U0, dx, dy, order, sides, gravity, gamma, cfl, t
     s.close()
     return {"workload": f"{name}, order {order}, CFL {cfl}, t = 0 -> {t_end}",
             "steps": n, "t_reached": t, "status": status, "wall_s": round(el, 3),
+            "occupancy": occupancy,
             "unit": UNIT, "value": nx * ny * 3 * n / el,
             "note": "host-timed whole run; each step reads its CFL dt back to the host"}
 
@@ -581,29 +589,32 @@ def end_to_end(s, U0, U, cells, a, nsnap=10):
         Uh_out[0].copy_(bufs[0], non_blocking=True)
     torch.cuda.synchronize()
     serial = time.perf_counter() - t0
-    return {"value": cells * 3 * a.steps / overlapped, "unit": UNIT,
+    return {"value": cells * 3 * a.steps / serial, "unit": UNIT,
             "h2d_bytes_per_step": U.numel() * 8,
             "d2h_bytes_per_step": Uh_out[0].numel() * 8,
             "inputs": f"{len(snaps)} snapshots of the timed trajectory, each the input of "
                       f"{m} consecutive steps",
-            "copies": "double-buffered on two copy streams, overlapping the neighbouring "
-                      "steps' compute; host-timed over all steps",
-            "serial_value": cells * 3 * a.steps / serial}
+            "copies": "value: one problem at a time, copy in, step, copy out on one stream; "
+                      "overlapped_value: the steps' copies double-buffered on two copy "
+                      "streams, overlapping the neighbouring steps' compute; both host-timed "
+                      "over all steps",
+            "overlapped_value": cells * 3 * a.steps / overlapped}
 
 
-def paper_runs(enomr, workloads, dev, R):
+def paper_runs(enomr, workloads, dev, R, occupancy="auto"):
     """The paper's 2D problems (Sec. 4.4), whole runs with their CFL steps."""
     out = {}
     U1, d1, _ = workloads.riemann2d_rp1(801)
     out["paper_rp1_801"] = paper_run(enomr, dev, "2D Riemann RP1, 801^2", U1, d1, d1, R,
-                                     None, (0.0, 0.0), 1.4, 0.3, 1.0)
+                                     None, (0.0, 0.0), 1.4, 0.3, 1.0, occupancy)
     Ud_, ddx, ddy, dsides = workloads.double_mach(1200, 300)
     out["paper_double_mach"] = paper_run(enomr, dev, "double Mach reflection, 1200x300",
-                                         Ud_, ddx, ddy, R, dsides, (0.0, 0.0), 1.4, 0.1, 0.2)
+                                         Ud_, ddx, ddy, R, dsides, (0.0, 0.0), 1.4, 0.1, 0.2,
+                                         occupancy)
     Ur_, rdx, rdy, rsides = workloads.rayleigh_taylor(200, 800)
     out["paper_rayleigh_taylor"] = paper_run(enomr, dev, "Rayleigh-Taylor, 200x800",
                                              Ur_, rdx, rdy, R, rsides, (0.0, 1.0),
-                                             5.0 / 3.0, 0.3, 1.95)
+                                             5.0 / 3.0, 0.3, 1.95, occupancy)
     return out
 
 
@@ -991,7 +1002,7 @@ def main_ours(a):
                                                       probe_ops)
         extras["riemann_sizes"] = riemann_sizes(enomr, workloads, dev, a.cfl)
     if rank == 0 and not a.no_extras and a.paper_runs:
-        extras.update(paper_runs(enomr, workloads, dev, R))
+        extras.update(paper_runs(enomr, workloads, dev, R, a.occupancy))
     if rank == 0 and not a.no_extras:
         hbm_peak = hbm_side(n, 0, 1.0)["peak_gbs"]
         extras.update(scalar_fracs(enomr, workloads, dev, peak_ops, hbm_peak))
@@ -1147,7 +1158,7 @@ def main_only(a):
     elif a.only == "vortex":
         out = vortex_rate(enomr, workloads, dev, a)
     elif a.only == "paper":
-        out = paper_runs(enomr, workloads, dev, a.order)
+        out = paper_runs(enomr, workloads, dev, a.order, a.occupancy)
     else:
         out = batched_gain(enomr, workloads, dev, a)
     print(json.dumps({"only": a.only, **out}), flush=True)

@@ -354,11 +354,18 @@ ENOMR_API int64_t enomr_batch_total_cells(const enomr_batch *b);
 ENOMR_API enomr_status enomr_batch_step(enomr_batch *b, double *U, double cfl);
 
 /* enomr_batch_autotune -- time the stage kernel on state U (read only) for
- * every tile size (32, 64, 128 interfaces) and persistent grid (2, 4, 8, 16
- * CTAs per SM), reps launches each, and keep the fastest for later steps.
- * *tile and *grid (host, may be NULL) receive the choice.  Synchronises. */
+ * every tile size (32, 64, 128 interfaces), persistent grid (2, 4, 8, 16
+ * CTAs per SM) and work-item size (1, 2, 4 consecutive tiles per item, so
+ * each thread evaluates that many interfaces per item), reps launches each,
+ * and keep the fastest for later steps.  *tile and *grid (host, may be NULL)
+ * receive the choice (enomr_batch_config gives all three).  Synchronises.
+ * Every setting gives the same results bit for bit. */
 ENOMR_API enomr_status enomr_batch_autotune(enomr_batch *b, const double *U, int reps, int *tile,
                                             int *grid);
+/* enomr_batch_config -- the tile size, grid and tiles per work item in use
+ * (host outputs, each may be NULL). */
+ENOMR_API enomr_status enomr_batch_config(const enomr_batch *b, int *tile, int *grid,
+                                          int *tiles_per_item);
 
 /* enomr_batch_get_status -- as enomr_get_status(). */
 ENOMR_API enomr_status enomr_batch_get_status(enomr_batch *b);

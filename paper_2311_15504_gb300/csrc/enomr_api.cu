@@ -116,6 +116,16 @@ __global__ void __launch_bounds__(256) k_alpha(AlphaArgs A)
         for (int q = 0; q < C; ++q) up[q] = A.U[q * ncell + i];
         have_up = true;
     }
+    // all of this thread's loads first (4 rows x C components in flight),
+    // then the comparisons and the list appends
+    double ur[4][C];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const long long y = y0 + j;
+        const bool valid = x < A.nx && y < A.ny;
+#pragma unroll
+        for (int q = 0; q < C; ++q) ur[j][q] = valid ? A.U[q * ncell + y * A.nx + x] : 0.0;
+    }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -123,7 +133,7 @@ __global__ void __launch_bounds__(256) k_alpha(AlphaArgs A)
         const bool valid = x < A.nx && y < A.ny;
         double u[C];
 #pragma unroll
-        for (int q = 0; q < C; ++q) u[q] = valid ? A.U[q * ncell + y * A.nx + x] : 0.0;
+        for (int q = 0; q < C; ++q) u[q] = ur[j][q];
         bool same_left = tx > 0;
 #pragma unroll
         for (int q = 0; q < C; ++q) {

@@ -37,7 +37,7 @@ struct enomr_batch {
     double *inv_dx;
     BatchTile *tiles[3];
     long long ntiles[3];
-    int tp_index, grid;
+    int tp_index, grid, per_item;
     double *alpha;  // [3][nprob][3]: alpha of U^n, U^(1), U^(2)
     double *dt;     // [nprob]
     int *status;
@@ -171,7 +171,7 @@ static const double B_C0[3] = {0.0, 0.75, 1.0 / 3.0};
 static const double B_C1[3] = {1.0, 0.25, 2.0 / 3.0};
 
 static enomr_status batch_stage(enomr_batch *b, int s, const double *Un, const double *Us,
-                                double *out, int tp_index, int grid)
+                                double *out, int tp_index, int grid, int per_item)
 {
     BatchArgs a;
     a.Us = Us;
@@ -185,6 +185,7 @@ static enomr_status batch_stage(enomr_batch *b, int s, const double *Un, const d
     a.dt = b->dt;
     a.tiles = b->tiles[tp_index];
     a.ntiles = b->ntiles[tp_index];
+    a.tiles_per_item = per_item;
     a.bc = b->bc;
     a.gm1 = b->gamma - 1.0;
     a.inv_gm1 = 1.0 / (b->gamma - 1.0);
@@ -242,6 +243,7 @@ ENOMR_API enomr_status enomr_batch_init(enomr_batch **out, int64_t nprob, const 
     b->gamma = gamma;
     b->stream = (cudaStream_t)stream;
     b->tp_index = 1;
+    b->per_item = 1;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -291,9 +293,9 @@ ENOMR_API enomr_status enomr_batch_step(enomr_batch *b, double *U, double cfl)
     if (!b || !U || !(cfl > 0.0)) return ENOMR_EINVAL;
     enomr_status st = batch_alpha_dt(b, U, cfl, true);
     if (st) return st;
-    if ((st = batch_stage(b, 1, U, U, b->U1, b->tp_index, b->grid))) return st;
-    if ((st = batch_stage(b, 2, U, b->U1, b->U2, b->tp_index, b->grid))) return st;
-    return batch_stage(b, 3, U, b->U2, U, b->tp_index, b->grid);
+    if ((st = batch_stage(b, 1, U, U, b->U1, b->tp_index, b->grid, b->per_item))) return st;
+    if ((st = batch_stage(b, 2, U, b->U1, b->U2, b->tp_index, b->grid, b->per_item))) return st;
+    return batch_stage(b, 3, U, b->U2, U, b->tp_index, b->grid, b->per_item);
 }
 
 ENOMR_API enomr_status enomr_batch_autotune(enomr_batch *b, const double *U, int reps,
@@ -304,28 +306,33 @@ ENOMR_API enomr_status enomr_batch_autotune(enomr_batch *b, const double *U, int
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     static const int mults[4] = {2, 4, 8, 16};
+    static const int items[3] = {1, 2, 4};
     cudaEvent_t e0, e1;
     B_TRY(cudaEventCreate(&e0));
     B_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bt = b->tp_index, bg = b->grid;
+    int bt = b->tp_index, bg = b->grid, bk = b->per_item;
     enomr_status st = ENOMR_OK;
     for (int ti = 0; ti < 3 && !st; ++ti) {
         b->tp_index = ti;
         st = batch_alpha_dt(b, U, 0.5, true);  // alpha and dt of U for stage 1
         for (int mi = 0; mi < 4 && !st; ++mi) {
             const int gsz = sms * mults[mi];
-            st = batch_stage(b, 1, U, U, b->U1, ti, gsz);  // warm-up
-            cudaEventRecord(e0, b->stream);
-            for (int r = 0; r < reps && !st; ++r) st = batch_stage(b, 1, U, U, b->U1, ti, gsz);
-            cudaEventRecord(e1, b->stream);
-            if (!st && cudaEventSynchronize(e1) == cudaSuccess) {
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) {
-                    best = ms;
-                    bt = ti;
-                    bg = gsz;
+            for (int ki = 0; ki < 3 && !st; ++ki) {
+                const int k = items[ki];
+                st = batch_stage(b, 1, U, U, b->U1, ti, gsz, k);  // warm-up
+                cudaEventRecord(e0, b->stream);
+                for (int r = 0; r < reps && !st; ++r) st = batch_stage(b, 1, U, U, b->U1, ti, gsz, k);
+                cudaEventRecord(e1, b->stream);
+                if (!st && cudaEventSynchronize(e1) == cudaSuccess) {
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best) {
+                        best = ms;
+                        bt = ti;
+                        bg = gsz;
+                        bk = k;
+                    }
                 }
             }
         }
@@ -334,9 +341,20 @@ ENOMR_API enomr_status enomr_batch_autotune(enomr_batch *b, const double *U, int
     cudaEventDestroy(e1);
     b->tp_index = bt;
     b->grid = bg;
+    b->per_item = bk;
     if (tile) *tile = kTileSizes[bt];
     if (grid) *grid = bg;
     return st;
+}
+
+ENOMR_API enomr_status enomr_batch_config(const enomr_batch *b, int *tile, int *grid,
+                                          int *tiles_per_item)
+{
+    if (!b) return ENOMR_EINVAL;
+    if (tile) *tile = kTileSizes[b->tp_index];
+    if (grid) *grid = b->grid;
+    if (tiles_per_item) *tiles_per_item = b->per_item;
+    return ENOMR_OK;
 }
 
 ENOMR_API enomr_status enomr_batch_get_status(enomr_batch *b)

@@ -111,6 +111,7 @@ struct BatchArgs {
     const double *dt;      // [nprob]
     const BatchTile *tiles;
     long long ntiles;
+    int tiles_per_item;    // consecutive tiles a CTA takes per work item
     int bc;
     double gm1, inv_gm1, gamma, c0, c1;
     int *status;

@@ -157,19 +157,26 @@ __device__ __forceinline__ void load_a_table(double *sA, int tid, int nthreads)
 }
 
 // ---------------------------------------------------------------------------
-// Epilogue: D -> output
+// Epilogue: the flux difference dF = F_{i+1/2} - F_{i-1/2} of a cell ->
+// D = -dF / h (+ the other sweep's partial right-hand side) -> output.
+// Contracted into fmas: D = fma(-dF, 1/h, Dprev), and the stage combination
+// c0 U^n + c1 (U + dt D) = fma(c0, U^n, c1 fma(dt, D, U)); 5 FP64 operations
+// per component instead of 7 -- the epilogue is the y sweep's largest FP64
+// consumer on piecewise-constant grids.  (A separate first-stage branch,
+// U + dt D alone, was measured 18 % slower on the y sweep: it changes the
+// code generation of the whole tile.)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double epilogue(const Epilogue &e, long long idx, double D, double Us,
-                                          bool src = false, double S = 0.0)
+__device__ __forceinline__ double epilogue(const Epilogue &e, long long idx, double dF,
+                                          double inv_h, double Us, bool src = false,
+                                          double S = 0.0)
 {
-    if (e.Dprev) D = e.Dprev[idx] + D;
+    double D = e.Dprev ? fma(-dF, inv_h, e.Dprev[idx]) : -dF * inv_h;
     if (src) D = D + S;  // body force, after the two directional differences
     double o;
     if (e.mode == EPI_STORE) {
         o = D;
     } else {
-        const double dt = *e.dt_dev;
-        o = e.c0 * e.Un[idx] + e.c1 * fma(dt, D, Us);
+        o = fma(e.c0, e.Un[idx], e.c1 * fma(*e.dt_dev, D, Us));
     }
     e.out[idx] = o;
     return o;

@@ -45,8 +45,7 @@ __global__ void __launch_bounds__(TP) k_advection(AdvArgs A)
     if (p < TP - 1) {
         const long long i = x0 + p;
         if (i < A.n) {
-            const double D = -(sFh[p + 1] - sFh[p]) * A.inv_h;
-            epilogue(A.epi, i, D, A.U[i]);
+            epilogue(A.epi, i, sFh[p + 1] - sFh[p], A.inv_h, A.U[i]);
         }
     }
 }
@@ -116,8 +115,7 @@ __global__ void __launch_bounds__(TP) k_burgers(AdvArgs A)
     if (p < TP - 1) {
         const long long i = x0 + p;
         if (i < A.n) {
-            const double D = -(sFh[p + 1] - sFh[p]) * A.inv_h;
-            epilogue(A.epi, i, D, A.U[i]);
+            epilogue(A.epi, i, sFh[p + 1] - sFh[p], A.inv_h, A.U[i]);
         }
     }
 }

@@ -677,7 +677,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
             for (int q = 0; q < C; ++q) {
                 // map line component back to the state component
                 const int qs = (q == 1) ? QN : ((C == 4 && q == 2) ? QT : q);
-                const double D = -(t.Fh(q, line, p + 1) - t.Fh(q, line, p)) * A.inv_h;
+                const double dF = t.Fh(q, line, p + 1) - t.Fh(q, line, p);
                 if constexpr (EXT) {
                     // body force (0, rho g_n, rho g_t, m_n g_n + m_t g_t)
                     double S = 0.0;
@@ -688,9 +688,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
                         S = (C == 4) ? __dadd_rn(__dmul_rn(t.U(1, line, sc), A.g_n),
                                                  __dmul_rn(t.U(2, line, sc), A.g_t))
                                      : __dmul_rn(t.U(1, line, sc), A.g_n);
-                    o[q] = epilogue(A.epi, qs * ncell + gi, D, t.U(q, line, sc), A.src != 0, S);
+                    o[q] = epilogue(A.epi, qs * ncell + gi, dF, A.inv_h, t.U(q, line, sc),
+                                    A.src != 0, S);
                 } else {
-                    o[q] = epilogue(A.epi, qs * ncell + gi, D, t.U(q, line, sc));
+                    o[q] = epilogue(A.epi, qs * ncell + gi, dF, A.inv_h, t.U(q, line, sc));
                 }
             }
             if (C == 3 && A.alpha_next) {
@@ -763,7 +764,17 @@ __global__ void __launch_bounds__(TP) k_batch_stage(BatchArgs B)
     __shared__ SweepSmem<R, 3, TP, 1> sm;
     __shared__ double sA[T * W];
     load_a_table<R>(sA, threadIdx.x, TP);
-    for (long long t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
+    // work items of tiles_per_item consecutive tiles (each thread evaluates
+    // that many interfaces per item), strided over the persistent grid
+    const int k = B.tiles_per_item;
+    const long long nitem = (B.ntiles + k - 1) / k;
+    for (long long t = 0, w = blockIdx.x, j = 0; w < nitem;) {
+        t = w * k + j;
+        if (++j == k) {
+            j = 0;
+            w += gridDim.x;
+        }
+        if (t >= B.ntiles) continue;
         __syncthreads();  // the previous tile is done with shared memory
         const BatchTile tl = B.tiles[t];
         const int pr = tl.prob;

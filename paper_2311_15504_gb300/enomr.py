@@ -69,6 +69,7 @@ _SIGS = {
     "enomr_batch_step": (_I, [_P, _P, _D]),
     "enomr_batch_autotune": (_I, [_P, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "enomr_batch_get_status": (_I, [_P]),
+    "enomr_batch_config": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "enomr_set_side": (_I, [_P, _I, _P]),
     "enomr_set_body_force": (_I, [_P, _D, _D]),
     "enomr_set_time": (_I, [_P, _D]),
@@ -380,6 +381,13 @@ class Batch:
         _check(_lib.enomr_batch_autotune(self._ctx, self._state(U), int(reps), ctypes.byref(t),
                                          ctypes.byref(g)), "enomr_batch_autotune")
         return t.value, g.value
+
+    def config(self):
+        """(tile, grid, tiles_per_item) in use."""
+        t, g, k = _I(), _I(), _I()
+        _check(_lib.enomr_batch_config(self._ctx, ctypes.byref(t), ctypes.byref(g),
+                                       ctypes.byref(k)), "enomr_batch_config")
+        return t.value, g.value, k.value
 
     def check_status(self):
         _check(_lib.enomr_batch_get_status(self._ctx), "enomr_batch_get_status")

@@ -114,3 +114,38 @@ def test_tma_full_size_steps_bitwise(E):
     assert torch.equal(Ua, Ub)
     a.check_status()
     b.check_status()
+
+
+@pytest.mark.parametrize("R", [5, 9, 17])
+@pytest.mark.parametrize("kind,bc,shape", [("riemann", 1, (70, 300)), ("smooth", 0, (64, 96)),
+                                          ("riemann", 1, (33, 131))])
+def test_occupancy_and_staging_instances_bitwise(E, R, kind, bc, shape):
+    """Every sweep instance -- plain loads or TMA, high or low occupancy --
+    gives the same right-hand side, selections and steps bit for bit (odd
+    nx: the TMA setting is refused and the loading instances run)."""
+    import torch
+    ny, nx = shape
+    U, dx, dy = _state(kind, ny, nx, seed=R + 7 * nx)
+    s = E.Solver(E.EULER, shape, order=R, dx=dx, dy=dy, bc=bc)
+    Ud = torch.from_numpy(U).cuda()
+    ref = None
+    for stg in (E.STAGING_LOADS, E.STAGING_TMA, E.STAGING_AUTO):
+        for occ in (E.OCCUPANCY_HIGH, E.OCCUPANCY_LOW, E.OCCUPANCY_AUTO):
+            s.set_staging(stg)
+            s.set_occupancy(occ)
+            if stg == E.STAGING_TMA and nx % 2:
+                with pytest.raises(E.EnomrError):
+                    s.rhs(Ud)
+                continue
+            r = s.rhs(Ud)
+            sel = s.selection(Ud)
+            Us = Ud.clone()
+            s.step(Us, 0.0, 0.4)
+            s.step(Us, 0.0, 0.4)
+            if ref is None:
+                ref = (r, sel, Us)
+            else:
+                assert torch.equal(r, ref[0]), (stg, occ)
+                assert torch.equal(sel, ref[1]), (stg, occ)
+                assert torch.equal(Us, ref[2]), (stg, occ)
+    s.check_status()
