@@ -264,7 +264,8 @@ ENOMR_API enomr_status enomr_set_staging(enomr_ctx *ctx, int mode);
  *                         of few tiles, whose launches last as long as a
  *                         few tiles in sequence;
  *   ENOMR_OCCUPANCY_AUTO  (default) LOW when the x sweep has fewer tiles
- *                         than two waves of the HIGH instance, else HIGH.
+ *                         than four waves of the HIGH instance (grids up to
+ *                         about 900^2), else HIGH.
  * On smooth data, where every interface takes the long path, LOW with TMA
  * staging is the fastest instance (about 4 % on a 4096^2 vortex); on
  * piecewise-constant data HIGH is (LOW is 40 % slower there).

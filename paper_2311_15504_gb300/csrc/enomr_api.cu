@@ -580,14 +580,17 @@ static bool extended(const enomr_ctx *c)
 }
 
 // The 2D sweeps' low-occupancy instances: forced, or (automatic) for grids
-// whose x sweep has fewer tiles than two waves of the high-occupancy
-// instance, where a launch's time is that of a few tiles in sequence.
+// whose x sweep has fewer tiles than four waves of the high-occupancy
+// instance.  Measured on GB300 (order 9): the paper's RP1 801^2 (3.7 waves),
+// double Mach reflection 1200x300 and Rayleigh-Taylor 200x800 whole runs
+// are 3-7 % faster with the low instance, the four-quadrant Riemann state at
+// 1024^2 (11 waves) and above is 30-40 % slower with it.
 static bool low_occupancy(const enomr_ctx *c)
 {
     if (c->occupancy == ENOMR_OCCUPANCY_LOW) return true;
     if (c->occupancy == ENOMR_OCCUPANCY_HIGH) return false;
     const long long tiles = ((c->nx + X_TP - 2) / (X_TP - 1)) * ((c->ny + X_NL - 1) / X_NL);
-    return tiles < 2LL * c->sms * (SWEEP_HIGH_THREADS_PER_SM / (X_TP * X_NL));
+    return tiles < 4LL * c->sms * (SWEEP_HIGH_THREADS_PER_SM / (X_TP * X_NL));
 }
 
 // Evaluate L(U) into the epilogue.  The alpha of U must be current.

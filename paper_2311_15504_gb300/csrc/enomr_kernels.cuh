@@ -159,18 +159,22 @@ __device__ __forceinline__ void load_a_table(double *sA, int tid, int nthreads)
 // ---------------------------------------------------------------------------
 // Epilogue: the flux difference dF = F_{i+1/2} - F_{i-1/2} of a cell ->
 // D = -dF / h (+ the other sweep's partial right-hand side) -> output.
-// Contracted into fmas: D = fma(-dF, 1/h, Dprev), and the stage combination
-// c0 U^n + c1 (U + dt D) = fma(c0, U^n, c1 fma(dt, D, U)); 5 FP64 operations
-// per component instead of 7 -- the epilogue is the y sweep's largest FP64
-// consumer on piecewise-constant grids.  (A separate first-stage branch,
-// U + dt D alone, was measured 18 % slower on the y sweep: it changes the
-// code generation of the whole tile.)
+// The stage combination is contracted, c0 U^n + c1 (U + dt D) =
+// fma(c0, U^n, c1 fma(dt, D, U)): 6 FP64 operations per component instead
+// of 7 (the epilogue is the y sweep's largest FP64 consumer on
+// piecewise-constant grids).  The two directional differences are added
+// with both rounded, D = Dprev + (-dF / h): a sum that commutes, so a state
+// symmetric under exchanging x and y keeps that symmetry bit for bit (an
+// fma there would round the two directions differently).  (A separate
+// first-stage branch, U + dt D alone, was measured 18 % slower on the y
+// sweep: it changes the code generation of the whole tile.)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double epilogue(const Epilogue &e, long long idx, double dF,
                                           double inv_h, double Us, bool src = false,
                                           double S = 0.0)
 {
-    double D = e.Dprev ? fma(-dF, inv_h, e.Dprev[idx]) : -dF * inv_h;
+    double D = -dF * inv_h;
+    if (e.Dprev) D = e.Dprev[idx] + D;
     if (src) D = D + S;  // body force, after the two directional differences
     double o;
     if (e.mode == EPI_STORE) {
