@@ -633,11 +633,12 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
                      state_map(c, U, 1, &my);
     if (c->staging == ENOMR_STAGING_TMA && !tma) return ENOMR_EINVAL;
     const bool low = low_occupancy(c);
-    // Automatic staging, per sweep (measured on GB300, 4096^2 Riemann and
-    // vortex states): the column sweep is faster with TMA at every order (its
-    // tile then has no bank conflicts); the row sweep loads its rows with
-    // plain coalesced loads up to order 13 and is faster with TMA from 15 on.
-    const bool tma_x = tma && (c->staging == ENOMR_STAGING_TMA || c->order >= 15);
+    // Automatic staging, per sweep (measured on GB300, 4096^2 Riemann
+    // state, orders 5-17): the column sweep is faster with TMA at every order
+    // (0.90 against 0.96 ms at order 9, 1.21 against 1.41 at 17; its tile
+    // then has no bank conflicts); the row sweep is faster with plain
+    // coalesced loads (0.71 against 0.79 ms at order 9, equal at 17).
+    const bool tma_x = tma && c->staging == ENOMR_STAGING_TMA;
     const bool tma_y = tma;
     SweepArgs ax = sweep_args(c, U, false);
     ax.sel = sel;

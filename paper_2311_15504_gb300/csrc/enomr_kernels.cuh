@@ -171,10 +171,13 @@ __device__ __forceinline__ void load_a_table(double *sA, int tid, int nthreads)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double epilogue(const Epilogue &e, long long idx, double dF,
                                           double inv_h, double Us, bool src = false,
-                                          double S = 0.0)
+                                          double S = 0.0, bool zero = false)
 {
-    double D = -dF * inv_h;
-    if (e.Dprev) D = e.Dprev[idx] + D;
+    // zero: the flux difference is exactly +0 (a tile on one state per
+    // line); then -dF / h is -0 and Dprev + (-0) is Dprev, bit for bit,
+    // without FP64 work
+    double D = zero ? -0.0 : -dF * inv_h;
+    if (e.Dprev) D = zero ? e.Dprev[idx] : e.Dprev[idx] + D;
     if (src) D = D + S;  // body force, after the two directional differences
     double o;
     if (e.mode == EPI_STORE) {

@@ -49,8 +49,7 @@ template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, bool low, cuda
     if (low)
         k_sweep<R, 4, 0, X_TP, X_NL, false, SWEEP_LOW_CTAS><<<grid_x(a), X_TP * X_NL, 0, s>>>(a);
     else
-        k_sweep<R, 4, 0, X_TP, X_NL, false, SWEEP_THREADS_PER_SM / (X_TP * X_NL), LONG_INLINE>
-            <<<grid_x(a), X_TP * X_NL, 0, s>>>(a);
+        k_sweep<R, 4, 0, X_TP, X_NL><<<grid_x(a), X_TP * X_NL, 0, s>>>(a);
     return cudaGetLastError();
 }
 

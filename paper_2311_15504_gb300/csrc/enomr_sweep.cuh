@@ -407,15 +407,23 @@ __device__ __noinline__ void long_tail(const SweepArgs &A, long long x0, long lo
 // All threads of the CTA must call it; it ends after its epilogue.
 // EXT: the 2D sweep with boundary sides and a body force (SweepArgs'
 // side_lo, side_hi, ..., src set); the plain instances leave them unread.
-// LM: form of the long path.  LONG_SPLIT (default): whole warps out of line
-// (long_path) and a partly filled last warp field-parallel (long_tail).
-// LONG_INLINE: every warp inline, interface-parallel -- the form measured
-// fastest for the plain-load row sweep of piecewise-constant grids, whose
-// code generation is sensitive to what surrounds its per-thread flat path.
-enum : int { LONG_INLINE = 0, LONG_SPLIT = 1 };
+// LM: form of the long path.  LONG_SPLIT: whole warps out of line
+// (long_path) and a partly filled last warp of at most LONG_TAIL interfaces
+// field-parallel (long_tail).  LONG_FIELDS: as LONG_SPLIT, and a whole list
+// of at most eight interfaces per warp field-parallel.  LONG_INLINE: every
+// warp inline, interface-parallel.  Measured on 4096^2 (piecewise-constant
+// state, order 9 / 17): the row sweep is fastest with LONG_FIELDS (0.76 /
+// 1.15 ms), the column sweep with LONG_SPLIT (0.93 / 1.30 ms against 0.97 /
+// 1.33 with LONG_FIELDS): its tiles hold four lines, so a front crossing
+// them fills its long-path warps better.
+enum : int { LONG_INLINE = 0, LONG_SPLIT = 1, LONG_FIELDS = 2 };
+template <int DIR>
+struct LongForm {
+    static constexpr int value = DIR == 0 ? LONG_FIELDS : LONG_SPLIT;
+};
 
-template <int R, int C, int DIR, int TP, int NL, bool EXT = false, int LM = LONG_SPLIT,
-          class Tile>
+template <int R, int C, int DIR, int TP, int NL, bool EXT = false,
+          int LM = LongForm<DIR>::value, class Tile>
 __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, long long l0,
                                            const double *sA, const Tile &t)
 {
@@ -450,6 +458,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
                            : NL == 8 ? 0x01010101u
                            : NL == 16 ? 0x00010001u : 0x00000001u;  // lanes of one line (DIR 1)
     const int lane = tid & 31;
+    bool varies_me = false;  // a cell differs from its predecessor in the same warp
     for (int base = tid & ~31; base < NS; base += NT) {
         const int idx = base + lane;
         const bool act = idx < NS;
@@ -493,6 +502,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
             same = same && (__double_as_longlong(pq) == __double_as_longlong(u[q]));
         }
         const bool rep = act && !same;
+        varies_me = varies_me || (rep && lane >= PD && s > 0);
         const unsigned reps = __ballot_sync(FULL, rep);
         // representative of this cell: the nearest representative lane at or
         // below this one on the same line (a line's first lane is one)
@@ -506,7 +516,37 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
             if (rep) t.slist()[b0 + __popc(reps & ((1u << lane) - 1u))] = (unsigned short)idx;
         }
     }
-    __syncthreads();
+    const bool varies = __syncthreads_or(varies_me) != 0;
+    // A tile whose every line holds one state (its halos included): every
+    // interface is flat on that line's state, its flux is the cell's flux and
+    // every flux difference is exactly zero, so the tile goes straight to
+    // its epilogue (most tiles of a piecewise-constant grid).  Only the
+    // representatives that start a warp's chunk of cells have not been
+    // compared with their predecessor yet.  (Selections or per-field values
+    // asked for, or forced choices: the full evaluation.)
+    bool constant = false;
+    if (!varies && !A.sel && !A.ft_out && !A.sel_in) {
+        bool bad = false;
+        const int nrep = t.nrep();
+        for (int j = tid; j < nrep; j += NT) {
+            const int idx = t.slist()[j];
+            int line, s;
+            if (DIR == 0) {
+                line = idx / S;
+                s = idx - line * S;
+            } else {
+                s = idx / NL;
+                line = idx - s * NL;
+            }
+            if (s > 0)
+#pragma unroll
+                for (int q = 0; q < C; ++q)
+                    bad = bad || __double_as_longlong(t.U(q, line, s)) !=
+                                     __double_as_longlong(t.U(q, line, s - 1));
+        }
+        constant = __syncthreads_or(bad) == 0;
+    }
+    if (!constant) {
     {
         const int nrep = t.nrep();
         for (int b = tid & ~31; b < nrep; b += NT) {
@@ -628,6 +668,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
         // pipe time and of the latency.
         const int n = t.nlist();
         int nip = n;
+        constexpr int NWARP = NT / 32;
         if constexpr (LM == LONG_INLINE) {
             for (int base = tid & ~31; base < n; base += NT) {
                 const int j = base + (tid & 31);
@@ -638,8 +679,15 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
             }
             nip = -1;  // done
         } else if constexpr (C == 4) {
+            // a list that fits eight interfaces per warp (a tile crossing a
+            // front) is evaluated field-parallel as a whole: its FP64 work is
+            // spread over every warp, and so over every sub-partition's FP64
+            // unit, instead of sitting in one or two warps
             const int r = n & 31;
-            if (r > 0 && r <= LONG_TAIL) nip = n - r;
+            if (LM == LONG_FIELDS && n <= 8 * NWARP)
+                nip = 0;
+            else if (r > 0 && r <= LONG_TAIL)
+                nip = n - r;
         }
         for (int base = tid & ~31; base < nip; base += NT) {
             const int j = base + (tid & 31);
@@ -649,9 +697,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
         }
         if (C == 4 && nip >= 0 && nip < n) {
             // the warps without a whole-warp chunk take the tail's chunks
-            constexpr int NW = NT / 32;
-            const int w0 = (nip >> 5) % NW, nchunk = (n - nip + 7) >> 3;
-            for (int c = ((tid >> 5) - w0 + NW) % NW; c < nchunk; c += NW) {
+            const int w0 = (nip >> 5) % NWARP, nchunk = (n - nip + 7) >> 3;
+            for (int c = ((tid >> 5) - w0 + NWARP) % NWARP; c < nchunk; c += NWARP) {
                 const int j = nip + c * 8 + (lane >> 2);
                 const bool act = j < n;
                 const int e = t.list()[act ? j : nip];
@@ -660,6 +707,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
         }
     }
     __syncthreads();
+    }  // !constant
 
     const int p = (DIR == 0) ? tid % TP : tid / NL;
     const int line = (DIR == 0) ? tid / TP : tid % NL;
@@ -677,7 +725,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
             for (int q = 0; q < C; ++q) {
                 // map line component back to the state component
                 const int qs = (q == 1) ? QN : ((C == 4 && q == 2) ? QT : q);
-                const double dF = t.Fh(q, line, p + 1) - t.Fh(q, line, p);
+                const double dF = constant ? 0.0 : t.Fh(q, line, p + 1) - t.Fh(q, line, p);
+                // (constant: the epilogue needs no FP64 for D, see epilogue())
                 if constexpr (EXT) {
                     // body force (0, rho g_n, rho g_t, m_n g_n + m_t g_t)
                     double S = 0.0;
@@ -689,9 +738,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
                                                  __dmul_rn(t.U(2, line, sc), A.g_t))
                                      : __dmul_rn(t.U(1, line, sc), A.g_n);
                     o[q] = epilogue(A.epi, qs * ncell + gi, dF, A.inv_h, t.U(q, line, sc),
-                                    A.src != 0, S);
+                                    A.src != 0, S, constant);
                 } else {
-                    o[q] = epilogue(A.epi, qs * ncell + gi, dF, A.inv_h, t.U(q, line, sc));
+                    o[q] = epilogue(A.epi, qs * ncell + gi, dF, A.inv_h, t.U(q, line, sc),
+                                    false, 0.0, constant);
                 }
             }
             if (C == 3 && A.alpha_next) {
@@ -739,7 +789,7 @@ constexpr int SWEEP_THREADS_PER_SM = SWEEP_HIGH_THREADS_PER_SM;
 constexpr int SWEEP_LOW_CTAS = 2;
 
 template <int R, int C, int DIR, int TP, int NL, bool EXT = false,
-          int MINB = SWEEP_THREADS_PER_SM / (TP * NL), int LM = LONG_SPLIT>
+          int MINB = SWEEP_THREADS_PER_SM / (TP * NL), int LM = LongForm<DIR>::value>
 __global__ void __launch_bounds__(TP *NL, MINB) k_sweep(SweepArgs A)
 {
     constexpr int g = (R + 1) / 2, W = 2 * g - 1, T = Tab<R>::T;
