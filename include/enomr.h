@@ -238,11 +238,10 @@ ENOMR_API enomr_status enomr_get_status(enomr_ctx *ctx);
 /*
  * enomr_set_staging -- how the 2D Euler sweeps bring a tile of cells (with
  * its g-cell halos, Sec. 2.1) into shared memory:
- *   ENOMR_STAGING_AUTO  (default) where the state allows TMA (nx even, U
- *                       16-byte aligned, no boundary sides or body force):
- *                       the column (y) sweep by TMA, the row (x) sweep with
- *                       plain loads (the faster of the two for each sweep
- *                       on GB300); otherwise plain loads;
+ *   ENOMR_STAGING_AUTO  (default) both sweeps by TMA where the state
+ *                       allows it (nx even, U 16-byte aligned, no boundary
+ *                       sides or body force; the faster staging for both
+ *                       sweeps on GB300), otherwise plain loads;
  *   ENOMR_STAGING_LOADS plain coalesced loads by the CTA's threads;
  *   ENOMR_STAGING_TMA   the TMA path only: calls whose state does not allow
  *                       it return ENOMR_EINVAL.

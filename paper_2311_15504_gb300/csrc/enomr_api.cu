@@ -81,16 +81,20 @@ namespace enomr {
 // changes none of its column's maxima.  So each row's maxima are attained
 // at a row representative (the first cell of its tile row, or one that
 // differs from its left neighbour) and each column's at a column
-// representative (likewise along the column); every other cell is skipped
-// (a constant region costs one evaluation per tile row and column), and so
-// is its status check, which its equal neighbour's covers.  The
+// representative (likewise along the column).  The neighbours are compared
+// across tile edges too (the column left of the tile and the row above it
+// are read for that), so the first cell of a run of equal cells along a
+// line, the one that carries the run's speeds, is the only representative
+// it needs, and a tile inside a constant region evaluates nothing.  Every
+// other cell is skipped, and so is its status check, which its equal
+// neighbour's covers.  The
 // representatives are compacted into a list that whole warps evaluate, so
 // skipped cells take no FP64 issue slots.  Every evaluated cell updates its
 // row, its column and the CFL maximum with its own speeds: the results are
 // the maxima over all cells, bit for bit.
 // ---------------------------------------------------------------------------
 template <int C>
-__global__ void __launch_bounds__(256) k_alpha(AlphaArgs A)
+__global__ void __launch_bounds__(256, 5) k_alpha(AlphaArgs A)
 {
     __shared__ unsigned long long srow[32][3], scol[32][3], scfl;
     __shared__ unsigned short list[1024];  // tile cell index: row * 32 + column
@@ -107,15 +111,21 @@ __global__ void __launch_bounds__(256) k_alpha(AlphaArgs A)
         scfl = 0;
         nlist = 0;
     }
-    // the cell above this thread's first row (inside the tile for ty > 0)
+    // the cell above this thread's first row (in the tile above for ty = 0)
     double up[C] = {};
     bool have_up = false;
-    if (C == 4 && ty > 0 && x < A.nx && y0 < A.ny) {
+    if (C == 4 && y0 > 0 && x < A.nx && y0 < A.ny) {
         const long long i = (y0 - 1) * A.nx + x;
 #pragma unroll
         for (int q = 0; q < C; ++q) up[q] = A.U[q * ncell + i];
         have_up = true;
     }
+    // the column left of the tile for this warp's rows: lane l < 4 C holds
+    // component l % C of row 4 ty + l / C
+    const long long xl = (long long)blockIdx.x * 32 - 1;
+    double lv = 0.0;
+    if (xl >= 0 && tx < 4 * C && y0 + tx / C < A.ny)
+        lv = A.U[(tx % C) * ncell + (y0 + tx / C) * A.nx + xl];
     // all of this thread's loads first (4 rows x C components in flight),
     // then the comparisons and the list appends
     double ur[4][C];
@@ -134,10 +144,12 @@ __global__ void __launch_bounds__(256) k_alpha(AlphaArgs A)
         double u[C];
 #pragma unroll
         for (int q = 0; q < C; ++q) u[q] = ur[j][q];
-        bool same_left = tx > 0;
+        bool same_left = tx > 0 || xl >= 0;
 #pragma unroll
         for (int q = 0; q < C; ++q) {
-            const double l = __shfl_up_sync(0xffffffffu, u[q], 1);
+            const double li = __shfl_up_sync(0xffffffffu, u[q], 1);
+            const double lo = __shfl_sync(0xffffffffu, lv, j * C + q);
+            const double l = tx > 0 ? li : lo;
             same_left = same_left && (__double_as_longlong(l) == __double_as_longlong(u[q]));
         }
         bool rep = valid && !same_left;
@@ -162,6 +174,7 @@ __global__ void __launch_bounds__(256) k_alpha(AlphaArgs A)
     }
     __syncthreads();
     const int n = nlist;
+    if (n == 0) return;  // every cell repeats one outside the tile
     for (int b = ty * 32; b < n; b += 256) {
         const int t = b + tx;
         if (t < n) {
@@ -633,12 +646,12 @@ static enomr_status rhs_with_epilogue(enomr_ctx *c, const double *U, const Epilo
                      state_map(c, U, 1, &my);
     if (c->staging == ENOMR_STAGING_TMA && !tma) return ENOMR_EINVAL;
     const bool low = low_occupancy(c);
-    // Automatic staging, per sweep (measured on GB300, 4096^2 Riemann
-    // state, orders 5-17): the column sweep is faster with TMA at every order
-    // (0.90 against 0.96 ms at order 9, 1.21 against 1.41 at 17; its tile
-    // then has no bank conflicts); the row sweep is faster with plain
-    // coalesced loads (0.71 against 0.79 ms at order 9, equal at 17).
-    const bool tma_x = tma && c->staging == ENOMR_STAGING_TMA;
+    // Automatic staging: TMA for both sweeps wherever the state allows it
+    // (measured on GB300, 4096^2 Riemann state, orders 5-17: faster at every
+    // order in both directions, e.g. row sweep 0.35 against 0.39 ms and
+    // column sweep 0.75 against 0.81 ms at order 9, 0.58 against 0.74 and
+    // 1.17 against 1.35 ms at order 17).
+    const bool tma_x = tma;
     const bool tma_y = tma;
     SweepArgs ax = sweep_args(c, U, false);
     ax.sel = sel;

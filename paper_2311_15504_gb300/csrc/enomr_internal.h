@@ -25,7 +25,8 @@ enum : unsigned long long { SGN_NEG = 1ULL, SGN_POS = 2ULL };
 // What a sweep does with its flux difference D_i = -(F_{i+1/2}-F_{i-1/2})/h.
 enum EpiMode : int {
     EPI_STORE = 0,   // out = D (+ Dprev)
-    EPI_STAGE = 1    // out = c0*Un + c1*(Us + dt*(D (+ Dprev)))
+    EPI_STAGE = 1,   // out = c0*Un + c1*(Us + dt*(D (+ Dprev)))
+    EPI_EULER = 2    // device form of EPI_STAGE with c0 = 0, c1 = 1: Us + dt*(D (+ Dprev))
 };
 
 struct Epilogue {

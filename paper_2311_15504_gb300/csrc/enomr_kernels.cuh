@@ -161,32 +161,74 @@ __device__ __forceinline__ void load_a_table(double *sA, int tid, int nthreads)
 // D = -dF / h (+ the other sweep's partial right-hand side) -> output.
 // The stage combination is contracted, c0 U^n + c1 (U + dt D) =
 // fma(c0, U^n, c1 fma(dt, D, U)): 6 FP64 operations per component instead
-// of 7 (the epilogue is the y sweep's largest FP64 consumer on
-// piecewise-constant grids).  The two directional differences are added
-// with both rounded, D = Dprev + (-dF / h): a sum that commutes, so a state
-// symmetric under exchanging x and y keeps that symmetry bit for bit (an
-// fma there would round the two directions differently).  (A separate
-// first-stage branch, U + dt D alone, was measured 18 % slower on the y
-// sweep: it changes the code generation of the whole tile.)
+// of 7.  The two directional differences are added with both rounded,
+// D = Dprev + (-dF / h): a sum that commutes, so a state symmetric under
+// exchanging x and y keeps that symmetry bit for bit (an fma there would
+// round the two directions differently).
+//
+// Forms.  The mode (store, or SSP-RK stage), whether an earlier sweep's
+// partial right-hand side is added, and (per CTA) whether the tile's flux
+// differences are all exactly zero are uniform, so each combination is
+// compiled as its own code and chosen by a branch outside the per-cell
+// code (with_epilogue_form).  Folded into one body with run-time tests,
+// the forms not taken are issued predicated off in every cell, and the FP64
+// pipe is charged per warp instruction whether or not a lane is on: in the
+// row sweep, whose form is always a plain store, the stage form's and the
+// sum's unused instructions took about three quarters of the FP64 issue.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double epilogue(const Epilogue &e, long long idx, double dF,
-                                          double inv_h, double Us, bool src = false,
-                                          double S = 0.0, bool zero = false)
+template <int V> struct IC {
+    static constexpr int value = V;
+};
+
+template <int MODE, bool PREV, bool ZERO>
+__device__ __forceinline__ double epilogue_form(const Epilogue &e, long long idx, double dF,
+                                               double inv_h, double Us, bool src, double S)
 {
-    // zero: the flux difference is exactly +0 (a tile on one state per
-    // line); then -dF / h is -0 and Dprev + (-0) is Dprev, bit for bit,
-    // without FP64 work
-    double D = zero ? -0.0 : -dF * inv_h;
-    if (e.Dprev) D = zero ? e.Dprev[idx] : e.Dprev[idx] + D;
+    double D;
+    if constexpr (ZERO) {
+        // the flux difference is exactly +0 (a tile on one state per line):
+        // -dF / h is -0 and Dprev + (-0) is Dprev, bit for bit, without FP64
+        D = PREV ? e.Dprev[idx] : -0.0;
+    } else {
+        D = -dF * inv_h;
+        if constexpr (PREV) D = e.Dprev[idx] + D;
+    }
     if (src) D = D + S;  // body force, after the two directional differences
     double o;
-    if (e.mode == EPI_STORE) {
+    if constexpr (MODE == EPI_STORE)
         o = D;
-    } else {
+    else if constexpr (MODE == EPI_EULER)
+        o = fma(*e.dt_dev, D, Us);
+    else
         o = fma(e.c0, e.Un[idx], e.c1 * fma(*e.dt_dev, D, Us));
-    }
     e.out[idx] = o;
     return o;
+}
+
+// Calls f(IC<form>, IC<prev>) with the launch's epilogue form.  A stage
+// with c0 = 0 and c1 = 1 (the first SSP-RK3 stage, the inner stages of the
+// linear SSP-RK(m, m-1) family) is a forward-Euler step, U + dt D, with one
+// FP64 operation per component instead of three: 1 * x is x, and
+// fma(0, U^n, x) is x for every finite U^n except that x = -0 comes out +0,
+// the one difference (a zero's sign) between the two forms.
+template <class F> __device__ __forceinline__ void with_epilogue_form(const Epilogue &e, F &&f)
+{
+    if (e.mode == EPI_STORE) {
+        if (e.Dprev)
+            f(IC<EPI_STORE>{}, IC<1>{});
+        else
+            f(IC<EPI_STORE>{}, IC<0>{});
+    } else if (e.c0 == 0.0 && e.c1 == 1.0) {
+        if (e.Dprev)
+            f(IC<EPI_EULER>{}, IC<1>{});
+        else
+            f(IC<EPI_EULER>{}, IC<0>{});
+    } else {
+        if (e.Dprev)
+            f(IC<EPI_STAGE>{}, IC<1>{});
+        else
+            f(IC<EPI_STAGE>{}, IC<0>{});
+    }
 }
 
 }  // namespace enomr

@@ -46,6 +46,7 @@ inline dim3 grid_y(const SweepArgs &a)
 
 template <int R> cudaError_t launch_euler2d_x(const SweepArgs &a, bool low, cudaStream_t s)
 {
+    if (!row_epilogue_ok(a)) return cudaErrorInvalidValue;
     if (low)
         k_sweep<R, 4, 0, X_TP, X_NL, false, SWEEP_LOW_CTAS><<<grid_x(a), X_TP * X_NL, 0, s>>>(a);
     else
@@ -68,6 +69,7 @@ template cudaError_t launch_euler1d<ENOMR_R>(const SweepArgs &, cudaStream_t);
 // with boundary sides / body force (the 2D problems of Sec. 4.4)
 template <int R> cudaError_t launch_euler2d_x_ext(const SweepArgs &a, bool low, cudaStream_t s)
 {
+    if (!row_epilogue_ok(a)) return cudaErrorInvalidValue;
     if (low)
         k_sweep<R, 4, 0, X_TP, X_NL, true, SWEEP_LOW_CTAS><<<grid_x(a), X_TP * X_NL, 0, s>>>(a);
     else

@@ -45,7 +45,10 @@ __global__ void __launch_bounds__(TP) k_advection(AdvArgs A)
     if (p < TP - 1) {
         const long long i = x0 + p;
         if (i < A.n) {
-            epilogue(A.epi, i, sFh[p + 1] - sFh[p], A.inv_h, A.U[i]);
+            with_epilogue_form(A.epi, [&](auto M, auto P) {
+                epilogue_form<decltype(M)::value, decltype(P)::value != 0, false>(
+                    A.epi, i, sFh[p + 1] - sFh[p], A.inv_h, A.U[i], false, 0.0);
+            });
         }
     }
 }
@@ -115,7 +118,10 @@ __global__ void __launch_bounds__(TP) k_burgers(AdvArgs A)
     if (p < TP - 1) {
         const long long i = x0 + p;
         if (i < A.n) {
-            epilogue(A.epi, i, sFh[p + 1] - sFh[p], A.inv_h, A.U[i]);
+            with_epilogue_form(A.epi, [&](auto M, auto P) {
+                epilogue_form<decltype(M)::value, decltype(P)::value != 0, false>(
+                    A.epi, i, sFh[p + 1] - sFh[p], A.inv_h, A.U[i], false, 0.0);
+            });
         }
     }
 }

@@ -721,29 +721,42 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &A, long long x0, lon
             const long long gi = (DIR == 0) ? Lg * nx + i : i * nx + Lg;
             const int sc = p + g;  // staged index of cell i
             double o[C];
+            auto cell = [&](auto M, auto P, auto Z) {
 #pragma unroll
-            for (int q = 0; q < C; ++q) {
-                // map line component back to the state component
-                const int qs = (q == 1) ? QN : ((C == 4 && q == 2) ? QT : q);
-                const double dF = constant ? 0.0 : t.Fh(q, line, p + 1) - t.Fh(q, line, p);
-                // (constant: the epilogue needs no FP64 for D, see epilogue())
-                if constexpr (EXT) {
-                    // body force (0, rho g_n, rho g_t, m_n g_n + m_t g_t)
+                for (int q = 0; q < C; ++q) {
+                    // map line component back to the state component
+                    const int qs = (q == 1) ? QN : ((C == 4 && q == 2) ? QT : q);
+                    double dF = 0.0;  // constant tile: exactly zero
+                    if constexpr (!decltype(Z)::value) dF = t.Fh(q, line, p + 1) - t.Fh(q, line, p);
                     double S = 0.0;
-                    const double rho = t.U(0, line, sc);
-                    if (q == 1) S = __dmul_rn(rho, A.g_n);
-                    if (C == 4 && q == 2) S = __dmul_rn(rho, A.g_t);
-                    if (q == C - 1)
-                        S = (C == 4) ? __dadd_rn(__dmul_rn(t.U(1, line, sc), A.g_n),
-                                                 __dmul_rn(t.U(2, line, sc), A.g_t))
-                                     : __dmul_rn(t.U(1, line, sc), A.g_n);
-                    o[q] = epilogue(A.epi, qs * ncell + gi, dF, A.inv_h, t.U(q, line, sc),
-                                    A.src != 0, S, constant);
-                } else {
-                    o[q] = epilogue(A.epi, qs * ncell + gi, dF, A.inv_h, t.U(q, line, sc),
-                                    false, 0.0, constant);
+                    if constexpr (EXT) {
+                        // body force (0, rho g_n, rho g_t, m_n g_n + m_t g_t)
+                        const double rho = t.U(0, line, sc);
+                        if (q == 1) S = __dmul_rn(rho, A.g_n);
+                        if (C == 4 && q == 2) S = __dmul_rn(rho, A.g_t);
+                        if (q == C - 1)
+                            S = (C == 4) ? __dadd_rn(__dmul_rn(t.U(1, line, sc), A.g_n),
+                                                     __dmul_rn(t.U(2, line, sc), A.g_t))
+                                         : __dmul_rn(t.U(1, line, sc), A.g_n);
+                    }
+                    o[q] = epilogue_form<decltype(M)::value, decltype(P)::value != 0,
+                                         decltype(Z)::value != 0>(
+                        A.epi, qs * ncell + gi, dF, A.inv_h, t.U(q, line, sc), EXT && A.src != 0,
+                        S);
                 }
-            }
+            };
+            auto tile_form = [&](auto M, auto P) {
+                if (constant)
+                    cell(M, P, IC<1>{});
+                else
+                    cell(M, P, IC<0>{});
+            };
+            // the 2D row sweep always stores its partial right-hand side
+            // (its launchers refuse any other epilogue)
+            if constexpr (DIR == 0 && C == 4)
+                tile_form(IC<EPI_STORE>{}, IC<0>{});
+            else
+                with_epilogue_form(A.epi, tile_form);
             if (C == 3 && A.alpha_next) {
                 double w3[3];
                 wave_speeds3(o[0], o[1], o[2], A.gm1, A.gamma, w3, A.status);
@@ -787,6 +800,14 @@ constexpr int SWEEP_THREADS_PER_SM = SWEEP_HIGH_THREADS_PER_SM;
 // without spilling; they serve launches of few tiles, whose speed is set by
 // the latency of one tile rather than by the number of warps in flight.
 constexpr int SWEEP_LOW_CTAS = 2;
+
+// The 2D row sweeps compile only the plain-store epilogue: their partial
+// right-hand side goes to a buffer that the column sweep adds.  Their
+// launchers refuse any other.
+inline bool row_epilogue_ok(const SweepArgs &a)
+{
+    return a.epi.mode == EPI_STORE && a.epi.Dprev == nullptr;
+}
 
 template <int R, int C, int DIR, int TP, int NL, bool EXT = false,
           int MINB = SWEEP_THREADS_PER_SM / (TP * NL), int LM = LongForm<DIR>::value>

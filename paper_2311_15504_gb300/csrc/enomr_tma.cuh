@@ -303,6 +303,7 @@ cudaError_t launch_sweep_tma(const CUtensorMap &map, const SweepArgs &a, cudaStr
 {
     using SM = TmaSmem<R, 4, DIR, TP, NL, SP>;
     using G = TmaGeom<R, DIR, TP, NL>;
+    if (DIR == 0 && !row_epilogue_ok(a)) return cudaErrorInvalidValue;
     constexpr int kMaxDev = 64;
     static int ctas[kMaxDev] = {}, sms[kMaxDev] = {};
     int dev = 0;
