@@ -190,10 +190,13 @@ __device__ __forceinline__ double epilogue_form(const Epilogue &e, long long idx
         // -dF / h is -0 and Dprev + (-0) is Dprev, bit for bit, without FP64
         D = PREV ? e.Dprev[idx] : -0.0;
     } else {
-        D = -dF * inv_h;
-        if constexpr (PREV) D = e.Dprev[idx] + D;
+        // explicitly rounded: with the product feeding the sum directly the
+        // compiler would contract them into an fma, and D_x + D_y would no
+        // longer commute
+        D = __dmul_rn(-dF, inv_h);
+        if constexpr (PREV) D = __dadd_rn(e.Dprev[idx], D);
     }
-    if (src) D = D + S;  // body force, after the two directional differences
+    if (src) D = __dadd_rn(D, S);  // body force, after the two directional differences
     double o;
     if constexpr (MODE == EPI_STORE)
         o = D;
