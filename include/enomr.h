@@ -110,8 +110,9 @@ ENOMR_API enomr_status enomr_rhs(enomr_ctx *ctx, const double *U, double *dUdt);
  *   s=1: Uout = Un + dt L(Un)                     (Us must equal Un)
  *   s=2: Uout = 3/4 Un + 1/4 (Us + dt L(Us))
  *   s=3: Uout = 1/3 Un + 2/3 (Us + dt L(Us))
- * The RHS is fused with the combination.  dt > 0 (host value).  Uout may
- * alias Un but not Us.
+ * The RHS is fused with the combination, rounded as written: stage 1 as
+ * fma(dt, L, Un), stages 2 and 3 as fma(c0, Un, c1 * fma(dt, L, Us)).
+ * dt > 0 (host value).  Uout may alias Un but not Us.
  */
 ENOMR_API enomr_status enomr_stage(enomr_ctx *ctx, int stage, const double *Un, const double *Us,
                                    double *Uout, double dt);
